@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds input GENERATORS only -- lattices, velocities, melts, meshes,
+deformation paths -- and none of the method's arithmetic (no forces, no
+integrator, no QR, no stress).  Both the CUDA path and the FP64 oracle are fed
+from here, so neither depends on the other.
+
+Workload recipes (the paper's own data are not available; these stand in):
+  * Cu-like FCC crystals (Sec. 2.1 uses a 10x10x10 FCC Cu cell, 4000 atoms,
+    edge 36.15 A): ``fcc(nx, ny, nz, a)`` with a = 3.615 A.
+  * Kremer-Grest melts (Sec. 2.2: linear bead-spring chains at melt density):
+    ``kg_melt(n_chains, chain_len, density, seed)`` -- seeded random walks with
+    bond length 0.97 sigma, then a displacement-capped soft push-off.
+  * Maxwell velocities with zero centre-of-mass momentum.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# CODATA 2018 exact / recommended values, used only to turn kT/m into a
+# velocity scale in metal units (Angstrom/ps).
+_EV = 1.602176634e-19
+_AMU = 1.66053906660e-27
+KB_EV = 8.617333262e-5  # Boltzmann constant, eV/K
+
+
+def vel_unit_sq(units: int) -> float:
+    """(energy / mass) expressed in (velocity unit)^2: metal eV/amu -> (A/ps)^2."""
+    return _EV / _AMU / 1e4 if units == 0 else 1.0
+
+
+def fcc(nx: int, ny: int, nz: int, a: float):
+    """FCC lattice of nx*ny*nz conventional cells; returns x (4 nx ny nz, 3) and H0 = diag(L)."""
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1).reshape(-1, 1, 3)
+    x = ((g + base[None]) * a).reshape(-1, 3)
+    H0 = np.diag([nx * a, ny * a, nz * a]).astype(np.float64)
+    return np.ascontiguousarray(x), H0
+
+
+def maxwell(n: int, mass: float, kT: float, units: int, seed: int):
+    """Seeded Maxwell-Boltzmann velocities at temperature kT with zero total momentum."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, 3)) * np.sqrt(kT * vel_unit_sq(units) / mass)
+    v -= v.mean(axis=0, keepdims=True)
+    return v
+
+
+def jitter(x: np.ndarray, amp: float, seed: int):
+    """Uniform random displacement of every coordinate in [-amp, amp]."""
+    rng = np.random.default_rng(seed)
+    return x + rng.uniform(-amp, amp, size=x.shape)
+
+
+def to_f32(a: np.ndarray) -> np.ndarray:
+    """Round to the FP32 grid (what the GPU stores), returned as float64."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def hex_mesh(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float):
+    """Structured 8-node hex mesh of a box [0,Lx]x[0,Ly]x[0,Lz]; node order per element
+    (-,-,-) (+,-,-) (+,+,-) (-,+,-) (-,-,+) (+,-,+) (+,+,+) (-,+,+)."""
+    xs, ys, zs = np.linspace(0, Lx, nx + 1), np.linspace(0, Ly, ny + 1), np.linspace(0, Lz, nz + 1)
+    X = np.stack(np.meshgrid(xs, ys, zs, indexing="ij"), -1).reshape(-1, 3)
+
+    def nid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    conn = []
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                conn.append([nid(i, j, k), nid(i + 1, j, k), nid(i + 1, j + 1, k), nid(i, j + 1, k),
+                             nid(i, j, k + 1), nid(i + 1, j, k + 1), nid(i + 1, j + 1, k + 1),
+                             nid(i, j + 1, k + 1)])
+    return np.ascontiguousarray(X), np.asarray(conn, dtype=np.int32)
+
+
+def uniaxial_bc(X: np.ndarray, L: float, all_nodes: bool = False):
+    """Boundary conditions for uniaxial extension along x (load factor = engineering strain).
+
+    all_nodes=True prescribes u = (lambda X_x, 0, 0) on every node (a single-element
+    uniaxial-strain test).  Otherwise: x=0 face u_x = 0, x=L face u_x = lambda L,
+    the node at the origin fully pinned, and the origin's x-edge neighbour on the
+    x=L face pinned in y and z (rigid-body modes); lateral faces free.
+    Returns (mask, val), each (nn, 3); prescribed d = lambda * val.
+    """
+    nn = X.shape[0]
+    mask = np.zeros((nn, 3), dtype=np.int32)
+    val = np.zeros((nn, 3))
+    if all_nodes:
+        mask[:] = 1
+        val[:, 0] = X[:, 0]
+        return mask, val
+    tol = 1e-9 * max(L, 1.0)
+    x0 = np.abs(X[:, 0]) < tol
+    xL = np.abs(X[:, 0] - L) < tol
+    mask[x0, 0] = 1
+    mask[xL, 0] = 1
+    val[xL, 0] = L
+    origin = np.where(x0 & (np.abs(X[:, 1]) < tol) & (np.abs(X[:, 2]) < tol))[0]
+    mask[origin, :] = 1
+    far = np.where(xL & (np.abs(X[:, 1]) < tol) & (np.abs(X[:, 2]) < tol))[0]
+    mask[far, 1] = 1
+    mask[far, 2] = 1
+    return mask, val
+
+
+def uniform_sizes(n_cells: int, lo: int, hi: int, multiple: int, seed: int):
+    """Uneven r-cell sizes: U[lo, hi] rounded down to a multiple of `multiple`."""
+    rng = np.random.default_rng(seed)
+    s = rng.integers(lo, hi + 1, size=n_cells)
+    return (s // multiple) * multiple
+
+
+def kg_melt(n_chains: int, chain_len: int, density: float, seed: int, bond: float = 0.97,
+            pushoff_iters: int = 300):
+    """Kremer-Grest style melt: seeded random-walk chains in a cubic box at the given
+    number density, followed by a displacement-capped push-off of overlapping
+    non-bonded beads (soft harmonic repulsion inside 1 sigma) that keeps bond
+    lengths near `bond`.  Returns x (N,3), H0, bonds (n_bonds, 2) int32.
+
+    This is input preparation, not the method: its only purpose is a start state
+    without overlaps, from which both the CUDA path and the oracle equilibrate.
+    """
+    rng = np.random.default_rng(seed)
+    n = n_chains * chain_len
+    L = (n / density) ** (1.0 / 3.0)
+    x = np.zeros((n, 3))
+    for c in range(n_chains):
+        p = rng.uniform(0, L, 3)
+        base = c * chain_len
+        x[base] = p
+        for k in range(1, chain_len):
+            while True:
+                u = rng.standard_normal(3)
+                u /= np.linalg.norm(u)
+                q = x[base + k - 1] + bond * u
+                if k < 2 or np.linalg.norm(q - x[base + k - 2]) > 1.02:
+                    break
+            x[base + k] = q
+    bonds = np.array([[c * chain_len + k, c * chain_len + k + 1]
+                      for c in range(n_chains) for k in range(chain_len - 1)], dtype=np.int32)
+    x = _pushoff(x, L, bonds, chain_len, pushoff_iters)
+    return np.ascontiguousarray(x), np.diag([L, L, L]), bonds
+
+
+def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
+    """Capped gradient steps on sum over non-bonded pairs of (rcut - r)^2 (r < rcut) plus
+    (r - bond)^2 springs on bonds; a cubic-box cell list in NumPy."""
+    n = x.shape[0]
+    nb = max(1, int(L // 1.0))
+    w = L / nb
+    bi, bj = bonds[:, 0], bonds[:, 1]
+    for _ in range(iters):
+        x = np.mod(x, L)
+        cid = np.minimum((x // w).astype(np.int64), nb - 1)
+        key = (cid[:, 0] * nb + cid[:, 1]) * nb + cid[:, 2]
+        order = np.argsort(key, kind="stable")
+        skey = key[order]
+        starts = np.searchsorted(skey, np.arange(nb ** 3))
+        ends = np.searchsorted(skey, np.arange(nb ** 3), side="right")
+        disp = np.zeros_like(x)
+        worst = 0.0
+        offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+        for (a, b, c) in offs:
+            nc = (cid + np.array([a, b, c])) % nb
+            nkey = (nc[:, 0] * nb + nc[:, 1]) * nb + nc[:, 2]
+            s, e = starts[nkey], ends[nkey]
+            cnt = e - s
+            mx = int(cnt.max()) if n else 0
+            for t in range(mx):
+                has = cnt > t
+                ii = np.nonzero(has)[0]
+                jj = order[s[ii] + t]
+                keep = jj != ii
+                same_chain_adjacent = (ii // chain_len == jj // chain_len) & (np.abs(ii - jj) == 1)
+                keep &= ~same_chain_adjacent
+                ii, jj = ii[keep], jj[keep]
+                d = x[ii] - x[jj]
+                d -= L * np.round(d / L)
+                r = np.linalg.norm(d, axis=1)
+                m = (r < rcut) & (r > 1e-12)
+                if np.any(m):
+                    worst = max(worst, float((rcut - r[m]).max()))
+                    np.add.at(disp, ii[m], (0.5 * (rcut - r[m]) / r[m])[:, None] * d[m])
+        d = x[bj] - x[bi]
+        d -= L * np.round(d / L)
+        r = np.linalg.norm(d, axis=1)
+        corr = (0.5 * (r - 0.97) / np.maximum(r, 1e-12))[:, None] * d
+        np.add.at(disp, bi, corr)
+        np.add.at(disp, bj, -corr)
+        nrm = np.linalg.norm(disp, axis=1, keepdims=True)
+        disp *= np.minimum(1.0, cap / np.maximum(nrm, 1e-300))
+        x = x + disp
+        if worst < 0.12:
+            break
+    return np.mod(x, L)
