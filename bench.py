@@ -1,0 +1,378 @@
+"""Benchmark of the r-cell hot path on GB300.
+
+Workload (default): the copper bar -- an 8x2x2 hex mesh, one quadrature point
+per element = 32 r-cells of 10x10x10 FCC copper (4000 atoms each, a = 3.615 A)
+with Sutton-Chen EAM (n = 9, m = 6, eps = 1.2382e-2 eV, c = 39.432, a = 3.61 A,
+rc = 2a), Maxwell velocities at 300 K, Langevin damping 0.1 ps, dt = 2 fs.
+Uniaxial tension to 5 % in 25 increments, 1000 MD steps per increment with the
+stress averaged over the last 500.
+
+One bench step = one FE load increment through the whole path: boundary
+conditions -> element F -> QR / box / remap -> 1000 MD steps (neighbour lists,
+density, forces, Verlet + Langevin, per-cell virial) -> time-averaged stress ->
+rotation and P -> FE internal force and explicit update.
+
+  value : atom-steps/s with everything resident in HBM (fe_step, device F).
+  e2e   : the same metric through the r-cell API with host buffers: each step
+          copies F from pinned host memory, runs the cells and copies sigma,
+          its standard error and P back (host<->device copies timed).
+
+`--impl reference` times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1902_09171_gb300 import inputs  # noqa: E402
+
+A_LAT = 3.615
+NC = 10                 # unit cells per edge of one r-cell
+MESH = (8, 2, 2)
+N_INC = 25
+STRAIN = 0.05
+MD_STEPS = 1000
+N_AVG = 500
+KT = 300 * inputs.KB_EV
+MASS = 63.546
+SC = dict(eps=1.2382e-2, a=3.61, rc=7.22, n=9.0, m=6.0, c=39.432)
+WORKLOAD = "copper_bar_sc_eam_32x4000"
+
+
+def make_cells(n_cells, seed0=1000):
+    x, H = inputs.fcc(NC, NC, NC, A_LAT)
+    x = inputs.to_f32(x)
+    return [dict(H0=H, x0=x, v0=inputs.to_f32(inputs.maxwell(len(x), MASS, KT, 0, seed0 + c))) for c in range(n_cells)]
+
+
+def mesh():
+    L = NC * A_LAT
+    X, conn = inputs.hex_mesh(*MESH, MESH[0] * L, MESH[1] * L, MESH[2] * L)
+    mask, val = inputs.uniaxial_bc(X, MESH[0] * L)
+    return X, conn, mask, val
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard(n_units, world, rank):
+    """Contiguous, balanced split of n_units independent units over ranks."""
+    base, extra = divmod(n_units, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp32_peak_tflops():
+    """FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128
+    FP32 lanes x 2 FLOP per FMA x 2070 MHz."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def sc_algorithmic_flops_per_atom_step(rho):
+    """Algorithmic FP32 work of one Sutton-Chen atom-step, counted once per
+    unordered pair inside rc (FMA = 2 FLOP): density pass 14 FLOP/pair, force
+    pass 44 FLOP/pair (see the design doc for the breakdown), plus 40 for the
+    integrator.  Returns (density_per_atom, force_per_atom, total_per_atom)."""
+    half_pairs = rho * 4.0 / 3.0 * np.pi * SC["rc"] ** 3 / 2.0
+    dens, force = 14.0 * half_pairs, 44.0 * half_pairs + 40.0
+    return dens, force, dens + force
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1902_09171_gb300 import build, rcell
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    rcell.load()
+    stream = torch.cuda.Stream()  # a dedicated stream: library kernels, flushes and events all on it
+    torch.cuda.set_stream(stream)
+    n_total = MESH[0] * MESH[1] * MESH[2]
+    # weak scaling: each rank runs a full copper bar (its own independent cells)
+    cells = make_cells(n_total, seed0=1000 + rank * n_total)
+    X, conn, mask, val = mesh()
+    prm = rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=12345 + rank, skin=args.skin)
+    ctx = rcell.rcell_create(prm, cells, stream=stream)
+    if args.tpa:
+        rcell.rcell_set_tuning(ctx, args.tpa, -1)
+    # FE: rho0 of copper in amu/A^3 (4 atoms per a^3), dt / damping in ps
+    rho0 = 4 * MASS / A_LAT ** 3
+    fe = rcell.fe_create(X, conn, mask, val, rho0, 0.05, 1.0, 0.0, stream=stream)
+    n_atoms = sum(len(c["x0"]) for c in cells)
+    md = args.md_steps
+    navg = min(N_AVG, md // 2)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_step(k):
+        lam = STRAIN * ((k % N_INC) + 1) / N_INC
+        rcell.fe_step(fe, ctx, lam, md, navg, None)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    if rcell.rcell_sync(ctx) != 0:
+        raise RuntimeError("warm-up failed: " + rcell.rcell_last_error(ctx))
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            one_step(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("timed run failed: " + rcell.rcell_last_error(ctx))
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    atom_steps = n_atoms * md * args.steps * world
+    value = atom_steps / (ms / 1e3)
+    launches_run = rcell.rcell_info(ctx)[2]
+    launches_per_step = launches_run + 2 + 1 + 4  # deform + remap, stress, FE (bc, F, fint, update)
+
+    # ---- e2e: host F in, host sigma / stderr / P out, through the r-cell API ----
+    pin = lambda shape: torch.zeros(shape, dtype=torch.float64).pin_memory()  # noqa: E731
+    F_h = pin((n_total, 3, 3))
+    sig_h, se_h, P_h = pin((n_total, 6)), pin((n_total, 6)), pin((n_total, 3, 3))
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        lam = STRAIN * ((k % N_INC) + 1) / N_INC
+        F_h.copy_(torch.from_numpy(np.tile(np.diag([1 + lam, 1 - 0.3 * lam, 1 - 0.3 * lam]), (n_total, 1, 1))))
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rcell.rcell_set_deformation(ctx, F_h)
+        rcell.rcell_run(ctx, md, navg)
+        rcell.rcell_stress(ctx, sig_h, se_h, P_h)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = atom_steps / (e2e_ms / 1e3)
+
+    # ---- per-kernel durations (CUDA events around each launch, same stream) ----
+    prof = rcell_kernel_profile(ctx, stream, n_steps=args.profile_steps)
+    rho = NC ** 3 * 4 / (NC * A_LAT) ** 3
+    dens_f, force_f, _ = sc_algorithmic_flops_per_atom_step(rho)
+    force_ms = prof["force"]
+    achieved = force_f * n_atoms / (force_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_force<SC> (force + Verlet/Langevin + virial)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)"}
+
+    rcell.fe_destroy(fe)
+    rcell.rcell_destroy(ctx)
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "atom-steps/s batched r-cell MD (copper bar, Sutton-Chen EAM, 32 x 4000 atoms)",
+            "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (pair math) / f64 (QR, remap, virial accumulation, FE)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": n_total * world, "atoms_per_cell": NC ** 3 * 4,
+                       "md_steps_per_increment": md, "n_avg": navg, "mesh": list(MESH), "l2": "flushed (256 MB write)",
+                       "parallelism": f"{world} independent cell batches" if world > 1 else "single GPU"},
+            "fe_load_steps_per_s": args.steps / (ms / 1e3),
+            "e2e": {"value": e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": int(F_h.numel() * 8),
+                    "d2h_bytes_per_step": int((sig_h.numel() + se_h.numel() + P_h.numel()) * 8)},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "kernel_ms": {k: round(v, 5) for k, v in prof.items()},
+            "roofline": roofline,
+            "clocks": clk.summary(),
+        }
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def rcell_kernel_profile(ctx, stream, n_steps=100):
+    """Mean duration of one launch of each kernel class over n_steps MD steps,
+    from CUDA events recorded around every launch on the library's stream."""
+    from paper_1902_09171_gb300 import rcell
+    return rcell.rcell_profile_kernels(ctx, n_steps)
+
+
+def run_oracle_sample(n_cells_sample, md_steps, threads):
+    """Time the FP64 oracle on a bounded sample of the workload: n_cells_sample
+    r-cells of the copper bar, one load increment each (QR, remap, md_steps MD
+    steps, stress), one cell per host thread.  Returns (atom_steps, seconds)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    cells = make_cells(n_cells_sample)
+    pot = oracle.pot_sc(SC["eps"], SC["a"], SC["rc"], SC["n"], SC["m"], SC["c"])
+    mdp = oracle.MD(0, MASS, KT, 0.1, 0.002, 12345)
+    lam = STRAIN / N_INC
+    F = np.diag([1 + lam, 1.0, 1.0])
+
+    def one(c):
+        Q, R = oracle.qr(F)
+        x = oracle.remap(cells[c]["x0"], oracle.delta_R(R, np.eye(3)))
+        _, _, _, ss, _, _ = oracle.md_run(pot, mdp, x, cells[c]["v0"], R @ cells[c]["H0"], cell=c, ev=0,
+                                          n_steps=md_steps, n_avg=md_steps // 2)
+        s_fem = np.array([oracle.rotate_pk1(Q, F, s)[0] for s in ss])
+        return s_fem.mean(0)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(n_cells_sample)))
+    dt = time.perf_counter() - t0
+    return n_cells_sample * len(cells[0]["x0"]) * md_steps, dt
+
+
+def cpu_baseline(target_s=15.0):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    threads = min(cores, MESH[0] * MESH[1] * MESH[2])
+    # calibrate: one cell, 2 steps
+    a, t = run_oracle_sample(1, 2, 1)
+    per_atom_step = t / a
+    steps = max(2, int(target_s * threads / (per_atom_step * 4000 * threads)))
+    steps = min(steps, MD_STEPS)
+    a, t = run_oracle_sample(threads, steps, threads)
+    return {"value": a / t, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{threads} of the 32 copper-bar r-cells (4000 atoms, Sutton-Chen), one increment of "
+                      f"{steps} MD steps each (QR, remap, MD, stress), one cell per host thread, FP64"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    threads = min(cores, MESH[0] * MESH[1] * MESH[2])
+    md = 3
+    for _ in range(args.warmup):
+        run_oracle_sample(threads, 1, threads)
+    tot_a, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        a, t = run_oracle_sample(threads, md, threads)
+        tot_a += a
+        tot_t += t
+    value = tot_a / tot_t
+    return {"impl": "reference", "metric": "atom-steps/s batched r-cell MD (copper bar, Sutton-Chen EAM, 32 x 4000 atoms)",
+            "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": MESH[0] * MESH[1] * MESH[2], "atoms_per_cell": NC ** 3 * 4},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step: {threads} r-cells x {md} MD steps (FP64 oracle)"},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--md-steps", type=int, default=MD_STEPS)
+    ap.add_argument("--skin", type=float, default=0.5)
+    ap.add_argument("--tpa", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_ours(args)
+    if out is not None:
+        if not args.no_cpu_baseline and out["n_gpus"] == 1:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

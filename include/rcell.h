@@ -1,0 +1,253 @@
+/*
+ * rcell.h -- C ABI of the GB300 r-cell engine for the hierarchical FEM <-> MD
+ * coupling of Murashima, Urata & Li (arXiv:1902.09171).
+ *
+ * Behind every finite-element quadrature point sits a representative cell
+ * (r-cell) of atoms.  Per load increment each r-cell takes the local
+ * deformation gradient F, splits it as F = Q R (Sec. 2.1), moves its atoms into
+ * the triangular box H_MD = R H(0) through Delta R = R(t) R(t-1)^{-1}
+ * (Eq. LAMMPS2), runs fixed-box MD, and returns its time-averaged virial stress
+ * rotated back to the FE frame (sigma_FEM = Q sigma_MD Q^T) together with the
+ * first Piola-Kirchhoff stress P = J sigma_FEM F^{-T} (Eq. Pmd) that the FE
+ * internal force (Eq. f) consumes.
+ *
+ * General rules for every call
+ *   - Return value: an rc_status code (RC_OK = 0).  Nothing aborts, throws
+ *     across the ABI or traps on the GPU.  After any error other than RC_ECUDA
+ *     the context stays usable; rcell_last_error() gives a one-line reason.
+ *   - The library owns all device memory it allocates (in rcell_create /
+ *     fe_create, plus lazily grown sample buffers in rcell_run).  The caller
+ *     owns every array it passes; inputs are copied before the call returns
+ *     (host inputs) or before the enqueued work reads them (device inputs must
+ *     stay valid until the stream reaches that work).
+ *   - All GPU work is enqueued on the CUDA stream given at creation (NULL =
+ *     the legacy default stream).  Calls marked "synchronous" wait for it.
+ *   - `where` arguments say whether a pointer is host memory (RC_HOST) or
+ *     device memory of the current device (RC_DEVICE).
+ *   - Matrices are row-major double[9] with F_iJ = dx_i / dX_J; a box matrix H
+ *     holds the three box vectors as COLUMNS (r = H s, Eq. LAMMPS1).
+ *   - Stresses are tension-positive Cauchy stresses in Voigt order
+ *     (xx, yy, zz, xy, xz, yz).  (Table 1 prints the opposite, pressure-like
+ *     sign.)  Units: GPa for RC_UNITS_METAL, eps/sigma^3 for RC_UNITS_LJ.
+ *   - Device-side failures (degenerate F, box too thin, broken bond, lost atom,
+ *     capacity overflow, non-finite energy) are recorded per cell in a status
+ *     word; they surface as the return value of the next synchronous call
+ *     (rcell_stress, rcell_sync, rcell_get_*).
+ */
+#ifndef RCELL_H
+#define RCELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rcell_ctx rcell_ctx; /* opaque: a batch of r-cells on one GPU   */
+typedef struct fe_ctx fe_ctx;       /* opaque: an explicit hex-8 FE mesh        */
+
+typedef enum {
+    RC_OK = 0,
+    RC_EINVAL = 1,     /* bad argument (null pointer, size, parameter)           */
+    RC_ENOMEM = 2,     /* device or host allocation failed                       */
+    RC_ECUDA = 3,      /* CUDA runtime error; the context may be unusable        */
+    RC_EDEGEN = 4,     /* det F <= 0: no rotation times positive stretch (Sec. 2.1) */
+    RC_EBOX = 5,       /* a perpendicular box width fell below 2 r_list           */
+    RC_EBOND = 6,      /* a FENE bond reached r >= R0                             */
+    RC_ELOST = 7,      /* an atom moved more than the skin within one step        */
+    RC_EOVERFLOW = 8,  /* neighbour / bin capacity exceeded                       */
+    RC_ENAN = 9,       /* non-finite force, energy or virial                      */
+    RC_ETIMEOUT = 10,  /* a bounded device-side wait gave up                      */
+    RC_ESTATE = 11     /* call out of order (e.g. stress before any run)          */
+} rc_status;
+
+enum { RC_HOST = 0, RC_DEVICE = 1 };
+enum { RC_POT_LJ = 0, RC_POT_SC = 1, RC_POT_KG = 2 };
+enum { RC_UNITS_METAL = 0, RC_UNITS_LJ = 1 };
+
+/* Interaction and integration parameters shared by every cell of a batch.
+ *   RC_POT_LJ : U = 4 eps [(sigma/r)^12 - (sigma/r)^6] for r < rc, unshifted.
+ *   RC_POT_SC : Sutton-Chen EAM, E = eps [1/2 sum_i sum_j!=i (a/r)^n
+ *               - c sum_i sqrt(rho_i)], rho_i = sum_j!=i (a/r)^m, r < rc;
+ *               `sigma` holds a.
+ *   RC_POT_KG : Kremer-Grest bead-spring (Sec. 2.2): LJ (eps, sigma, rc) between
+ *               non-bonded pairs; bonded pairs get FENE
+ *               -1/2 k_fene R0^2 ln(1 - (r/R0)^2) plus WCA (LJ cut and shifted
+ *               at 2^{1/6} sigma) and no non-bonded LJ.
+ * Integration: velocity Verlet with time step dt; force-form Langevin
+ * thermostat with damping time tau (tau <= 0: none), temperature kT (energy
+ * units), noise from Philox4x32-10 keyed by `seed`.  skin: Verlet-list skin
+ * (r_list = rc + skin); lists are rebuilt when an atom has moved more than
+ * skin/2 since the last build. */
+typedef struct {
+    int potential;       /* RC_POT_*                                           */
+    int units;           /* RC_UNITS_*                                         */
+    double eps, sigma, rc;
+    double n, m, c;      /* Sutton-Chen                                        */
+    double k_fene, R0;   /* Kremer-Grest bonds                                 */
+    double skin;
+    double mass, kT, tau, dt;
+    uint64_t seed;
+} rcell_params;
+
+/* One r-cell's initial state (host memory).
+ *   H0     : 9 doubles, upper-triangular initial box (the paper's H(0) is
+ *            orthogonal; a diagonal H0 is the usual case).
+ *   x0, v0 : 3 n_atoms doubles, Cartesian positions / velocities (atom-major).
+ *   bonds  : 2 n_bonds ints, 0-based atom indices (RC_POT_KG only; at most 4
+ *            bonds per atom).
+ * Atom index ("tag") order of x0 is the order every per-atom output uses. */
+typedef struct {
+    int n_atoms;
+    const double *H0;
+    const double *x0;
+    const double *v0;
+    int n_bonds;
+    const int *bonds;
+} rcell_init;
+
+/* Create a batch of n_cells r-cells (uneven atom counts allowed) on the current
+ * CUDA device.  stream: a cudaStream_t (NULL = default stream).  Copies all
+ * inputs; *out receives the context.  Errors: RC_EINVAL (bad sizes/params,
+ * box thinner than 2 r_list), RC_ENOMEM, RC_ECUDA.  Synchronous. */
+int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cells, void *stream, rcell_ctx **out);
+
+/* Sec. 2.1 + Eq. LAMMPS2: for every cell c take F_c (n_cells x 9 doubles,
+ * row-major), factor F = Q R with R_ii > 0 (FP64 Gram-Schmidt on the GPU),
+ * set the box to R H0, remap atom positions x <- (R R_prev^{-1}) x (FP64 math on
+ * the FP32 positions; velocities unchanged) and schedule a neighbour rebuild.
+ * where: location of F.  Cells with det F <= 0 get RC_EDEGEN and keep their
+ * previous state; cells whose new box is thinner than 2 r_list get RC_EBOX.
+ * Asynchronous. */
+int rcell_set_deformation(rcell_ctx *ctx, const double *F, int where);
+
+/* Run n_steps fixed-box MD steps on every cell (one setup force evaluation +
+ * n_steps velocity-Verlet steps) and record the instantaneous virial stress of
+ * the last n_avg steps (0 <= n_avg <= n_steps).  Captured into a CUDA graph
+ * per (n_steps, n_avg) after its first use.  Asynchronous. */
+int rcell_run(rcell_ctx *ctx, int n_steps, int n_avg);
+
+/* Time-averaged stress of the last rcell_run, per cell:
+ *   sigma        n_cells x 6: mean of Q sigma_MD(t) Q^T over the sampled steps
+ *                (sigma_MD(t) = -(sum m v (x) v + W(t)) / det H, W the pair virial);
+ *   sigma_stderr n_cells x 6 or NULL: blocking standard error of that mean
+ *                (largest over blocking levels that keep >= 16 blocks);
+ *   P            n_cells x 9 or NULL: P = J sigma F^{-T} (Eq. Pmd).
+ * All outputs in `where` memory.  Synchronous when where == RC_HOST; returns
+ * the first per-cell error status, or RC_ESTATE if no samples exist. */
+int rcell_stress(rcell_ctx *ctx, double *sigma, double *sigma_stderr, double *P, int where);
+
+/* Evaluate conservative forces, potential energy and pair virial at the current
+ * positions (no integration, no thermostat), rebuilding lists as needed.
+ * Results are read with rcell_get_atoms / rcell_get_energy.  Asynchronous. */
+int rcell_eval(rcell_ctx *ctx);
+
+/* Per-cell potential energy and pair virial W (9, row-major, compression-
+ * positive) of the last rcell_eval, host memory (n_cells and n_cells x 9;
+ * either may be NULL).  Synchronous. */
+int rcell_get_energy(rcell_ctx *ctx, double *pe, double *W);
+
+/* Copy one cell's per-atom state to host memory in tag order: positions
+ * (wrapped into the current box), velocities, and the forces of the last
+ * rcell_eval (any pointer may be NULL; 3 n_atoms doubles each).  Synchronous. */
+int rcell_get_atoms(rcell_ctx *ctx, int cell, double *x, double *v, double *f);
+
+/* Current MD box (9 doubles, upper triangular) and the Q, R of the last
+ * deformation (9 each); any may be NULL.  Host memory.  Synchronous. */
+int rcell_get_box(rcell_ctx *ctx, int cell, double *H, double *Q, double *R);
+
+/* Neighbour list of one cell as ordered tag pairs (i, j): every pair whose
+ * distance (with its periodic image) was below r_list at the last list build.
+ * pairs: 2 * max_pairs ints (host); *count receives the number of pairs
+ * (RC_EOVERFLOW if it exceeds max_pairs).  Synchronous. */
+int rcell_get_neighbors(rcell_ctx *ctx, int cell, int *pairs, long max_pairs, long *count);
+
+/* Per-step samples of the last rcell_run for one cell (host memory, n_avg
+ * entries each, any may be NULL): MD-frame stress (n_avg x 6), potential
+ * energy, kinetic energy.  Synchronous. */
+int rcell_get_series(rcell_ctx *ctx, int cell, double *stress, double *pe, double *ke);
+
+/* Wait for the stream; return the first per-cell error (or RC_OK). */
+int rcell_sync(rcell_ctx *ctx);
+
+/* Clear the per-cell error words (after the caller has handled them). */
+int rcell_clear_status(rcell_ctx *ctx);
+
+/* Tuning knobs (chosen by the autotuner; any value < 0 keeps the current):
+ *   threads_per_atom : 1, 2, 4 or 8 lanes cooperate on one atom's neighbours
+ *   use_graphs       : 0/1, capture rcell_run into CUDA graphs */
+int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
+
+/* Number of cells, total atoms, and the number of kernels the last rcell_run
+ * enqueued (for launch accounting); any pointer may be NULL. */
+int rcell_info(const rcell_ctx *ctx, int *n_cells, long *n_atoms, long *launches_last_run);
+
+/* Measurement helper: run n_steps more MD steps (plus a re-application of the
+ * current F and a stress reduction) launching kernels one by one, with CUDA
+ * events on the context's stream around every launch; ms_out (8 host doubles)
+ * receives the mean duration in ms of one launch of: neighbour sort, list
+ * build, Sutton-Chen density pass, force/integrate kernel (steady-state steps),
+ * deformation (QR/box), remap, stress reduction, other (0 when not launched).
+ * Advances the MD state like rcell_run.  Synchronous. */
+int rcell_profile_kernels(rcell_ctx *ctx, int n_steps, double *ms_out);
+
+/* Per-cell checkpoint (the state the MD engine keeps between FE steps, Sec. 2.1:
+ * positions, velocities, box, previous stretch R(t-1), random-stream counter).
+ * rcell_checkpoint with buf == NULL returns the needed size in *bytes.  Host
+ * buffers; synchronous.  rcell_restore requires the same atom count.  Both
+ * schedule a neighbour rebuild for the cell, so a run after rcell_restore
+ * repeats bit for bit the run that followed rcell_checkpoint. */
+int rcell_checkpoint(rcell_ctx *ctx, int cell, void *buf, size_t *bytes);
+int rcell_restore(rcell_ctx *ctx, int cell, const void *buf, size_t bytes);
+
+/* One-line description of the last error on this context (never NULL). */
+const char *rcell_last_error(const rcell_ctx *ctx);
+
+/* Free all device and host memory of the context (NULL is allowed). */
+void rcell_destroy(rcell_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Explicit finite elements (Sec. 2.2, Eq. f): 8-node hexahedra with one
+ * centroid quadrature point (one r-cell per element), lumped mass
+ * M = sum_e rho0 V_e / 8 per node, Flanagan-Belytschko stiffness hourglass
+ * control (coefficient hg_coef, stiffness hg_coef V_e^{1/3}), mass-
+ * proportional damping, central-difference update with time step dt.
+ *   X       : nn x 3 reference coordinates (host)
+ *   hex     : ne x 8 node ids (host), node order (-,-,-) (+,-,-) (+,+,-) (-,+,-)
+ *             (-,-,+) (+,-,+) (+,+,+) (-,+,+) in natural coordinates
+ *   bc_mask : nn x 3 ints, nonzero = prescribed DOF (host)
+ *   bc_val  : nn x 3 doubles; prescribed displacement = lambda * bc_val (host)
+ * ------------------------------------------------------------------------- */
+int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mask, const double *bc_val,
+              double rho0, double dt, double damping, double hg_coef, void *stream, fe_ctx **out);
+
+/* Set the prescribed DOFs to lambda * bc_val.  Asynchronous. */
+int fe_apply_bc(fe_ctx *fe, double lambda);
+
+/* Element deformation gradients F_e = I + sum_a d_a (x) grad_X N_a (ne x 9) into
+ * `where` memory.  Synchronous when where == RC_HOST. */
+int fe_get_F(fe_ctx *fe, double *F, int where);
+
+/* Explicit update from element first Piola-Kirchhoff stresses P (ne x 9, in
+ * `where` memory): assemble f_int (Eq. f, plus hourglass), then on free DOFs
+ * v <- ((1 - c dt/2) v + dt (-f_int/m)) / (1 + c dt/2), d <- d + dt v.
+ * Asynchronous. */
+int fe_update(fe_ctx *fe, const double *P, int where);
+
+/* One multiscale FE step (Fig. 1 of the paper): apply the BCs at lambda, compute
+ * F_e, hand them to the r-cells (rcell_set_deformation), run n_steps MD steps
+ * averaging the last n_avg, take P from rcell_stress, update the FE mesh.  The
+ * r-cell batch must hold one cell per element.  u_out: nn x 3 host doubles or
+ * NULL (synchronous when given).  Everything else stays on the device. */
+int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, double *u_out);
+
+/* Displacements and velocities (nn x 3 each, host; either may be NULL). */
+int fe_get_state(fe_ctx *fe, double *d, double *v);
+
+void fe_destroy(fe_ctx *fe);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCELL_H */

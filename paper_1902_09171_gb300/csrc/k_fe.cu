@@ -1,0 +1,150 @@
+// Explicit finite elements in FP64 (Sec. 2.2, Eq. f): 8-node hexahedra, one
+// centroid quadrature point per element (one r-cell each), lumped mass,
+// Flanagan-Belytschko stiffness hourglass control, damped central-difference
+// update.  One thread per element / per DOF; nodal sums by FP64 atomics.
+#include "rc_internal.cuh"
+
+namespace {
+
+// natural coordinates of the 8 nodes: (-,-,-) (+,-,-) (+,+,-) (-,+,-) (-,-,+) (+,-,+) (+,+,+) (-,+,+)
+__constant__ signed char c_nat[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                        {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+__global__ void k_geometry(const double *__restrict__ X, const int *__restrict__ conn, int ne, double rho0,
+                           double *gradN, double *V0, double *mass, int *err) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    // J_{i alpha} = sum_a X_{a i} dN_a/dxi_alpha, dN_a/dxi_alpha = nat_a,alpha / 8 at the centroid
+    double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < 8; a++) {
+        const double *Xa = X + 3 * conn[8 * e + a];
+        for (int i = 0; i < 3; i++)
+            for (int al = 0; al < 3; al++) J[3 * i + al] += Xa[i] * 0.125 * c_nat[a][al];
+    }
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    if (!(det > 0.0)) {
+        atomicExch(err, 1);
+        return;
+    }
+    double Ji[9];
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    // grad_X N_a = J^{-T} dN_a/dxi
+    for (int a = 0; a < 8; a++)
+        for (int k = 0; k < 3; k++) {
+            double s = 0.0;
+            for (int al = 0; al < 3; al++) s += Ji[3 * al + k] * 0.125 * c_nat[a][al];
+            gradN[24 * e + 3 * a + k] = s;
+        }
+    const double V = 8.0 * det;
+    V0[e] = V;
+    for (int a = 0; a < 8; a++) atomicAdd(&mass[conn[8 * e + a]], rho0 * V / 8.0);
+}
+
+__global__ void k_apply_bc(const int *__restrict__ mask, const double *__restrict__ val, double lambda, double *d,
+                           int n3) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n3 && mask[q]) d[q] = lambda * val[q];
+}
+
+__global__ void k_F(const int *__restrict__ conn, const double *__restrict__ gradN, const double *__restrict__ d,
+                    double *F, int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    double G[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int a = 0; a < 8; a++) {
+        const double *da = d + 3 * conn[8 * e + a];
+        const double *ga = gradN + 24 * e + 3 * a;
+        for (int i = 0; i < 3; i++)
+            for (int J = 0; J < 3; J++) G[3 * i + J] += da[i] * ga[J];
+    }
+    for (int k = 0; k < 9; k++) F[9 * e + k] = G[k];
+}
+
+// f_int,a = V0 P grad N_a + kappa sum_alpha gamma_{alpha a} q_alpha, kappa = hg V0^{1/3},
+// gamma_{alpha a} = (h_{alpha a} - (sum_b h_{alpha b} X_b) . grad N_a) / 8,
+// h = (eta zeta, zeta xi, xi eta, xi eta zeta) at the nodes, q_alpha = sum_b gamma_{alpha b} d_b.
+__global__ void k_fint(const double *__restrict__ X, const int *__restrict__ conn, const double *__restrict__ gradN,
+                       const double *__restrict__ V0, const double *__restrict__ P, const double *__restrict__ d,
+                       double hg, double *fint, int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const double *g = gradN + 24 * e, *Pe = P + 9 * e;
+    const double V = V0[e];
+    double fe[24];
+    for (int a = 0; a < 8; a++)
+        for (int i = 0; i < 3; i++)
+            fe[3 * a + i] = V * (Pe[3 * i] * g[3 * a] + Pe[3 * i + 1] * g[3 * a + 1] + Pe[3 * i + 2] * g[3 * a + 2]);
+    if (hg != 0.0) {
+        const double kappa = hg * cbrt(V);
+        for (int al = 0; al < 4; al++) {
+            double h[8], hX[3] = {0, 0, 0};
+            for (int a = 0; a < 8; a++) {
+                const int x = c_nat[a][0], y = c_nat[a][1], z = c_nat[a][2];
+                h[a] = al == 0 ? y * z : al == 1 ? z * x : al == 2 ? x * y : x * y * z;
+                const double *Xa = X + 3 * conn[8 * e + a];
+                hX[0] += h[a] * Xa[0];
+                hX[1] += h[a] * Xa[1];
+                hX[2] += h[a] * Xa[2];
+            }
+            double gam[8], q[3] = {0, 0, 0};
+            for (int a = 0; a < 8; a++) {
+                gam[a] = 0.125 * (h[a] - (hX[0] * g[3 * a] + hX[1] * g[3 * a + 1] + hX[2] * g[3 * a + 2]));
+                const double *da = d + 3 * conn[8 * e + a];
+                q[0] += gam[a] * da[0];
+                q[1] += gam[a] * da[1];
+                q[2] += gam[a] * da[2];
+            }
+            for (int a = 0; a < 8; a++)
+                for (int i = 0; i < 3; i++) fe[3 * a + i] += kappa * gam[a] * q[i];
+        }
+    }
+    for (int a = 0; a < 8; a++)
+        for (int i = 0; i < 3; i++) atomicAdd(&fint[3 * conn[8 * e + a] + i], fe[3 * a + i]);
+}
+
+__global__ void k_update(const int *__restrict__ mask, const double *__restrict__ mass, const double *__restrict__ fint,
+                         double dt, double damping, double *d, double *v, int n3) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n3) return;
+    if (mask[q]) {
+        v[q] = 0.0;
+        return;
+    }
+    const double c0 = 1.0 - 0.5 * damping * dt, c1 = 1.0 + 0.5 * damping * dt;
+    const double acc = -fint[q] / mass[q / 3];
+    const double vn = (c0 * v[q] + dt * acc) / c1;
+    v[q] = vn;
+    d[q] += dt * vn;
+}
+
+}  // namespace
+
+void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
+                        double *mass, int *err, cudaStream_t s) {
+    k_geometry<<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
+}
+void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
+                        cudaStream_t s) {
+    (void)v;
+    k_apply_bc<<<(n3 + 255) / 256, 256, 0, s>>>(mask, val, lambda, d, n3);
+}
+void fe_launch_F(const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s) {
+    k_F<<<(ne + 127) / 128, 128, 0, s>>>(conn, gradN, d, F, ne);
+}
+void fe_launch_fint(const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
+                    const double *d, double hg, double *fint, int ne, cudaStream_t s) {
+    k_fint<<<(ne + 127) / 128, 128, 0, s>>>(X, conn, gradN, V0, P, d, hg, fint, ne);
+}
+void fe_launch_update(const int *mask, const double *mass, const double *fint, double dt, double damping, double *d,
+                      double *v, int n3, cudaStream_t s) {
+    k_update<<<(n3 + 255) / 256, 256, 0, s>>>(mask, mass, fint, dt, damping, d, v, n3);
+}

@@ -1,0 +1,346 @@
+// Force evaluation fused with the velocity-Verlet / Langevin update and the
+// per-cell virial reduction -- one launch per MD step (two for Sutton-Chen,
+// whose embedding term needs every rho_i before any force).
+//
+// Thread mapping: a CTA owns one tile of RC_TILE atoms of one r-cell; TPA
+// consecutive lanes share one atom and split its Verlet list (TPA in 1,2,4,8),
+// combining their partial sums with xor-shuffles.  Neighbour positions are
+// gathered as float4 (16-byte, read-only path); atoms of a cell are stored
+// bin-sorted, so the gathers of a warp hit a few L1/L2 lines.
+//
+// Arithmetic: pair math in FP32 (fused multiply-adds); per-atom virial and
+// energy partials in FP32; per-warp sums promoted to FP64 before the per-cell
+// atomic accumulation.
+//
+// Per step (mode STEP): f(t) from x(t); v(t) = v(t-dt/2) + dt/2 a(t) with
+// a = f/m - v/tau + noise (Langevin friction on the velocity held at force
+// time); sample K = sum m v(t) (x) v(t), W(t), PE(t); then v(t+dt/2) = v(t) +
+// dt/2 a(t), x(t+dt) = x(t) + dt v(t+dt/2) written to the other position
+// buffer, and the skin test that schedules the next neighbour rebuild.
+#include "rc_internal.cuh"
+
+namespace {
+
+template <int TPA>
+__device__ __forceinline__ float sub_sum(float v) {
+#pragma unroll
+    for (int d = 1; d < TPA; d <<= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Sutton-Chen density pass: rho_i = sum_j (a/r_ij)^m over r < rc; writes
+// xr_i = {x_i, rho_i^{-1/2}} for the force pass.
+template <int TPA, bool M6>
+__global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, int cur) {
+    const int t = blockIdx.x;
+    const int c = a.tile_cell[t];
+    if (a.status[c] != 0) return;
+    __shared__ float3 s_shift[27];
+    __shared__ float s_H[8];
+    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
+    __syncthreads();
+
+    const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
+    const int n = a.cell_n[c], off = a.cell_off[c];
+    const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
+    const float4 *__restrict__ X = cur ? a.x1 : a.x0;
+    const bool live = li < n;
+    const int g = off + li;
+    float rho = 0.0f;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        xi = X[g];
+        const int nn = a.nnb[g];
+        const int *__restrict__ nb = a.nbr + (size_t)t * p.max_nb * RC_TILE + at;
+        const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m;
+        for (int k = sub; k < nn; k += TPA) {
+            const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
+            const float4 xj = __ldg(X + (e & RC_IDX_MASK));
+            const float3 sh = s_shift[e >> RC_IDX_BITS];
+            const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < p.rc2) {
+                const float ar2 = a2 * __fdividef(1.0f, r2);
+                rho += M6 ? ar2 * ar2 * ar2 : powf(ar2, hm);
+            }
+        }
+    }
+    rho = sub_sum<TPA>(rho);
+    if (live && sub == 0) a.xr[g] = make_float4(xi.x, xi.y, xi.z, rho > 0.0f ? rsqrtf(rho) : 0.0f);
+}
+
+// Block reduction of NV per-atom float values into FP64, then one atomicAdd per
+// value into dst[0..NV).
+template <int NV, int NT>
+__device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
+    __shared__ double s_part[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        float x = v[k];
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+        if (lane == 0) s_part[warp][k] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; w++) s += s_part[w][threadIdx.x];
+        atomicAdd(dst + threadIdx.x, s);
+    }
+}
+
+template <int POT, int TPA, bool M6>
+__global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, int cur, int mode, int slot,
+                                                       int step_index) {
+    const int t = blockIdx.x;
+    const int c = a.tile_cell[t];
+    if (a.status[c] != 0) return;
+    __shared__ float3 s_shift[27];
+    __shared__ float s_H[8];
+    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
+    __syncthreads();
+
+    const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
+    const int n = a.cell_n[c], off = a.cell_off[c];
+    const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
+    const bool live = li < n;
+    const int g = off + li;
+    const float4 *__restrict__ X = cur ? a.x1 : a.x0;
+    const float4 *__restrict__ XG = (POT == RC_POT_SC) ? a.xr : X;  // gathered array
+
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;  // xx yy zz xy xz yz
+    float pe = 0.f;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        xi = XG[g];
+        const int nn = a.nnb[g];
+        const int *__restrict__ nb = a.nbr + (size_t)t * p.max_nb * RC_TILE + at;
+        if (POT == RC_POT_SC) {
+            const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m, hn = 0.5f * p.sc_n;
+            const float cm2 = 0.5f * p.sc_c * p.sc_m;
+            for (int k = sub; k < nn; k += TPA) {
+                const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
+                const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
+                const float3 sh = s_shift[e >> RC_IDX_BITS];
+                const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < p.rc2) {
+                    const float ir2 = __fdividef(1.0f, r2);
+                    const float ar2 = a2 * ir2;
+                    float arm, arn;
+                    if (M6) {
+                        arm = ar2 * ar2 * ar2;                     // (a/r)^6
+                        arn = arm * ar2 * (p.sigma * rsqrtf(r2));  // (a/r)^9
+                    } else {
+                        arm = powf(ar2, hm);
+                        arn = powf(ar2, hn);
+                    }
+                    // dE/dr / r = eps / r^2 [ -n (a/r)^n + c m/2 (rho_i^-1/2 + rho_j^-1/2) (a/r)^m ]
+                    const float gr = p.eps * ir2 * fmaf(cm2 * (xi.w + xj.w), arm, -p.sc_n * arn);
+                    fx = fmaf(gr, dx, fx);
+                    fy = fmaf(gr, dy, fy);
+                    fz = fmaf(gr, dz, fz);
+                    const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
+                    w0 = fmaf(hx, dx, w0);
+                    w1 = fmaf(hy, dy, w1);
+                    w2 = fmaf(-0.5f * gr * dz, dz, w2);
+                    w3 = fmaf(hx, dy, w3);
+                    w4 = fmaf(hx, dz, w4);
+                    w5 = fmaf(hy, dz, w5);
+                    pe = fmaf(0.5f * p.eps, arn, pe);
+                }
+            }
+        } else {
+            const float s2 = p.sigma * p.sigma;
+            const float c24 = 24.0f * p.eps, c2 = 2.0f * p.eps;
+            for (int k = sub; k < nn; k += TPA) {
+                const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
+                const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
+                const float3 sh = s_shift[e >> RC_IDX_BITS];
+                const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < p.rc2) {
+                    const float ir2 = __fdividef(1.0f, r2);
+                    const float sr2 = s2 * ir2;
+                    const float sr6 = sr2 * sr2 * sr2;
+                    // dU/dr / r = -24 eps (2 (s/r)^12 - (s/r)^6) / r^2
+                    const float gr = -c24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
+                    fx = fmaf(gr, dx, fx);
+                    fy = fmaf(gr, dy, fy);
+                    fz = fmaf(gr, dz, fz);
+                    const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
+                    w0 = fmaf(hx, dx, w0);
+                    w1 = fmaf(hy, dy, w1);
+                    w2 = fmaf(-0.5f * gr * dz, dz, w2);
+                    w3 = fmaf(hx, dy, w3);
+                    w4 = fmaf(hx, dz, w4);
+                    w5 = fmaf(hy, dz, w5);
+                    pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
+                }
+            }
+        }
+    }
+    fx = sub_sum<TPA>(fx);
+    fy = sub_sum<TPA>(fy);
+    fz = sub_sum<TPA>(fz);
+    w0 = sub_sum<TPA>(w0);
+    w1 = sub_sum<TPA>(w1);
+    w2 = sub_sum<TPA>(w2);
+    w3 = sub_sum<TPA>(w3);
+    w4 = sub_sum<TPA>(w4);
+    w5 = sub_sum<TPA>(w5);
+    pe = sub_sum<TPA>(pe);
+    const bool own = live && sub == 0;
+
+    if (own && POT == RC_POT_SC && xi.w > 0.0f) pe -= p.eps * p.sc_c / xi.w;  // embedding -eps c sqrt(rho_i)
+
+    if (own && POT == RC_POT_KG) {
+        // FENE + WCA on the (at most four) bond partners; each bond is seen from
+        // both ends, so each end takes half of the virial and energy.
+        const int4 pr = a.partner[g];
+        const int q[4] = {pr.x, pr.y, pr.z, pr.w};
+        const float *Hi = a.Hif + 8 * c;
+#pragma unroll
+        for (int b = 0; b < RC_MAX_BONDS; b++) {
+            if (q[b] < 0) continue;
+            const float4 xj = X[off + q[b]];
+            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            // minimum image through fractional coordinates
+            float s2_ = Hi[5] * dz, s1_ = Hi[3] * dy + Hi[4] * dz, s0_ = Hi[0] * dx + Hi[1] * dy + Hi[2] * dz;
+            s0_ = rintf(s0_);
+            s1_ = rintf(s1_);
+            s2_ = rintf(s2_);
+            dx -= s_H[0] * s0_ + s_H[1] * s1_ + s_H[2] * s2_;
+            dy -= s_H[3] * s1_ + s_H[4] * s2_;
+            dz -= s_H[5] * s2_;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 < p.R02)) {
+                rc_set_status(a.status, c, RC_EBOND);
+                continue;
+            }
+            const float ratio = r2 / p.R02;
+            float gr = p.k_fene / (1.0f - ratio);
+            float U = -0.5f * p.k_fene * p.R02 * log1pf(-ratio);
+            if (r2 < p.wca2) {
+                const float sr2 = p.sigma * p.sigma / r2, sr6 = sr2 * sr2 * sr2;
+                gr -= 24.0f * p.eps * sr6 * (2.0f * sr6 - 1.0f) / r2;
+                U += 4.0f * p.eps * sr6 * (sr6 - 1.0f) + p.eps;
+            }
+            fx = fmaf(gr, dx, fx);
+            fy = fmaf(gr, dy, fy);
+            fz = fmaf(gr, dz, fz);
+            const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
+            w0 = fmaf(hx, dx, w0);
+            w1 = fmaf(hy, dy, w1);
+            w2 = fmaf(-0.5f * gr * dz, dz, w2);
+            w3 = fmaf(hx, dy, w3);
+            w4 = fmaf(hx, dz, w4);
+            w5 = fmaf(hy, dz, w5);
+            pe += 0.5f * U;
+        }
+    }
+
+    if (mode == MODE_EVAL) {
+        if (own) a.f[g] = make_float4(fx, fy, fz, pe);
+        float v[7] = {own ? pe : 0.f, own ? w0 : 0.f, own ? w1 : 0.f, own ? w2 : 0.f,
+                      own ? w3 : 0.f, own ? w4 : 0.f, own ? w5 : 0.f};
+        block_reduce_add<7, RC_TILE * TPA>(v, a.eval_acc + 8 * c);
+        return;
+    }
+
+    // ---- velocity Verlet + Langevin ----
+    float kxx = 0.f, kyy = 0.f, kzz = 0.f, kxy = 0.f, kxz = 0.f, kyz = 0.f;
+    if (own) {
+        float4 vv = a.v[g];
+        float ax = fx * p.fm, ay = fy * p.fm, az = fz * p.fm;
+        if (p.inv_tau > 0.0f) {
+            const float3 z = rc_normals3((unsigned)a.tag[g], (unsigned)c, a.evals[c] + (unsigned long long)step_index,
+                                         p.seed);
+            ax += fmaf(-vv.x, p.inv_tau, p.noise * z.x);
+            ay += fmaf(-vv.y, p.inv_tau, p.noise * z.y);
+            az += fmaf(-vv.z, p.inv_tau, p.noise * z.z);
+        }
+        const float hdt = 0.5f * p.dt;
+        if (mode != MODE_SETUP) {  // complete v(t)
+            vv.x = fmaf(hdt, ax, vv.x);
+            vv.y = fmaf(hdt, ay, vv.y);
+            vv.z = fmaf(hdt, az, vv.z);
+            kxx = p.mvv2e * vv.x * vv.x;
+            kyy = p.mvv2e * vv.y * vv.y;
+            kzz = p.mvv2e * vv.z * vv.z;
+            kxy = p.mvv2e * vv.x * vv.y;
+            kxz = p.mvv2e * vv.x * vv.z;
+            kyz = p.mvv2e * vv.y * vv.z;
+        }
+        if (mode == MODE_LAST) {
+            a.v[g] = vv;
+        } else {
+            vv.x = fmaf(hdt, ax, vv.x);
+            vv.y = fmaf(hdt, ay, vv.y);
+            vv.z = fmaf(hdt, az, vv.z);
+            float4 xn = make_float4(fmaf(p.dt, vv.x, xi.x), fmaf(p.dt, vv.y, xi.y), fmaf(p.dt, vv.z, xi.z), 0.0f);
+            a.v[g] = vv;
+            (cur ? a.x0 : a.x1)[g] = xn;
+            const float4 xr0 = a.xref[g];
+            const float ddx = xn.x - xr0.x, ddy = xn.y - xr0.y, ddz = xn.z - xr0.z;
+            const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (d2 > p.skin_half2) a.need_rebuild[c] = 1;
+            const float step2 = p.dt * p.dt * (vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
+            if (!(step2 <= p.skin_half2)) rc_set_status(a.status, c, isfinite(step2) ? RC_ELOST : RC_ENAN);
+        }
+    }
+    if (slot >= 0) {
+        float v[13] = {kxx, kyy, kzz, kxy, kxz, kyz,
+                       own ? w0 : 0.f, own ? w1 : 0.f, own ? w2 : 0.f, own ? w3 : 0.f, own ? w4 : 0.f, own ? w5 : 0.f,
+                       own ? pe : 0.f};
+        block_reduce_add<13, RC_TILE * TPA>(v, a.series + ((size_t)c * a.series_cap + slot) * RC_SAMPLE_W);
+    }
+}
+
+template <int POT, bool M6>
+void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
+                      int step_index, cudaStream_t s) {
+    switch (tpa) {
+    case 1: k_force<POT, 1, M6><<<n_tiles, RC_TILE * 1, 0, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 2: k_force<POT, 2, M6><<<n_tiles, RC_TILE * 2, 0, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 4: k_force<POT, 4, M6><<<n_tiles, RC_TILE * 4, 0, s>>>(p, a, cur, mode, slot, step_index); break;
+    default: k_force<POT, 8, M6><<<n_tiles, RC_TILE * 8, 0, s>>>(p, a, cur, mode, slot, step_index); break;
+    }
+}
+
+template <bool M6>
+void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s) {
+    switch (tpa) {
+    case 1: k_density<1, M6><<<n_tiles, RC_TILE * 1, 0, s>>>(p, a, cur); break;
+    case 2: k_density<2, M6><<<n_tiles, RC_TILE * 2, 0, s>>>(p, a, cur); break;
+    case 4: k_density<4, M6><<<n_tiles, RC_TILE * 4, 0, s>>>(p, a, cur); break;
+    default: k_density<8, M6><<<n_tiles, RC_TILE * 8, 0, s>>>(p, a, cur); break;
+    }
+}
+
+}  // namespace
+
+void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s) {
+    if (p.sc_m == 6.0f) launch_density_m<true>(p, a, cur, n_tiles, tpa, s);
+    else launch_density_m<false>(p, a, cur, n_tiles, tpa, s);
+}
+
+void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
+                     int step_index, cudaStream_t s) {
+    const bool m69 = p.sc_m == 6.0f && p.sc_n == 9.0f;
+    if (p.pot == RC_POT_SC) {
+        if (m69) launch_force_pot<RC_POT_SC, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+        else launch_force_pot<RC_POT_SC, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+    } else if (p.pot == RC_POT_KG) {
+        launch_force_pot<RC_POT_KG, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+    } else {
+        launch_force_pot<RC_POT_LJ, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+    }
+}

@@ -1,0 +1,234 @@
+// Neighbour-list build for triclinic r-cells (one list per cell, all cells of a
+// batch in one launch).
+//
+//  k_sort  : one CTA per r-cell.  Wraps positions into the current box through
+//            fractional coordinates, bins atoms on an n0 x n1 x n2 grid over the
+//            fractional cube (n_d = floor(w_d / r_list), w_d the perpendicular
+//            width), counting-sorts them by bin (stable, so the order is
+//            deterministic) and permutes every per-atom array.
+//  k_nlist : one thread per atom.  Scans the 27 neighbour bins with explicit
+//            periodic image shifts; with n_d >= 2 (guaranteed by w_d >= 2 r_list)
+//            each (bin, image) pair is visited once, so each (j, image) within
+//            r_list is stored exactly once.
+#include "rc_internal.cuh"
+
+namespace {
+
+constexpr int SORT_THREADS = 1024;
+
+// exclusive scan of s[0..n) in place (n <= RC_MAX_BINS_PER_CELL), returns total
+__device__ int block_exclusive_scan(int *s, int n) {
+    __shared__ int warp_tot[SORT_THREADS / 32];
+    const int per = (n + SORT_THREADS - 1) / SORT_THREADS;
+    const int lo = threadIdx.x * per;
+    int local = 0;
+    for (int k = 0; k < per; k++)
+        if (lo + k < n) local += s[lo + k];
+    // inclusive warp scan of `local`
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int v = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += y;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int excl = v - local + (warp > 0 ? warp_tot[warp - 1] : 0);
+    int total = warp_tot[31];
+    __syncthreads();
+    int run = excl;
+    for (int k = 0; k < per; k++)
+        if (lo + k < n) {
+            int c = s[lo + k];
+            s[lo + k] = run;
+            run += c;
+        }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int cur) {
+    const int c = blockIdx.x;
+    __shared__ int s_cnt[RC_MAX_BINS_PER_CELL];
+    __shared__ int s_go;
+    if (threadIdx.x == 0) {
+        int go = a.need_rebuild[c] && a.status[c] == 0;
+        a.built[c] = go;
+        if (go) a.need_rebuild[c] = 0;
+        s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+
+    const int n = a.cell_n[c], off = a.cell_off[c];
+    const int nb0 = a.nbins[4 * c], nb1 = a.nbins[4 * c + 1], nb2 = a.nbins[4 * c + 2];
+    const int nbt = nb0 * nb1 * nb2;
+    const float *H = a.Hf + 8 * c, *Hi = a.Hif + 8 * c;
+    const float h00 = H[0], h01 = H[1], h02 = H[2], h11 = H[3], h12 = H[4], h22 = H[5];
+    const float i00 = Hi[0], i01 = Hi[1], i02 = Hi[2], i11 = Hi[3], i12 = Hi[4], i22 = Hi[5];
+    float4 *X = cur ? a.x1 : a.x0;
+    const bool kg = p.pot == RC_POT_KG;
+
+    for (int b = threadIdx.x; b < nbt; b += SORT_THREADS) s_cnt[b] = 0;
+    __syncthreads();
+
+    // pass A: wrap, bin, stage a copy of every per-atom array
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const int g = off + i;
+        float4 x = X[g];
+        float s2 = i22 * x.z, s1 = i11 * x.y + i12 * x.z, s0 = i00 * x.x + i01 * x.y + i02 * x.z;
+        float f0 = floorf(s0), f1 = floorf(s1), f2 = floorf(s2);
+        float w0 = s0 - f0, w1 = s1 - f1, w2 = s2 - f2;
+        float xw = x.x - (h00 * f0 + h01 * f1 + h02 * f2);
+        float yw = x.y - (h11 * f1 + h12 * f2);
+        float zw = x.z - h22 * f2;
+        int b0 = min(max((int)(w0 * nb0), 0), nb0 - 1);
+        int b1 = min(max((int)(w1 * nb1), 0), nb1 - 1);
+        int b2 = min(max((int)(w2 * nb2), 0), nb2 - 1);
+        int bin = (b0 * nb1 + b1) * nb2 + b2;
+        a.x_tmp[g] = make_float4(xw, yw, zw, 0.0f);
+        a.binid[g] = bin;
+        a.v_tmp[g] = a.v[g];
+        a.tag_tmp[g] = a.tag[g];
+        if (kg) a.partner_tmp[g] = a.partner[g];
+        atomicAdd(&s_cnt[bin], 1);
+    }
+    __syncthreads();
+
+    block_exclusive_scan(s_cnt, nbt);
+    int *bs = a.bin_start + a.bin_off[c];
+    for (int b = threadIdx.x; b < nbt; b += SORT_THREADS) bs[b] = s_cnt[b];
+    if (threadIdx.x == 0) bs[nbt] = n;
+    __syncthreads();
+
+    // stable ranking inside bins: one warp walks the atoms in their current order
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < n;
+            const int bin = valid ? a.binid[off + i] : -1 - lane;
+            const unsigned m = __match_any_sync(0xffffffffu, bin);
+            const int leader = __ffs(m) - 1;
+            int start = 0;
+            if (valid && lane == leader) {
+                start = s_cnt[bin];
+                s_cnt[bin] = start + __popc(m);
+            }
+            start = __shfl_sync(0xffffffffu, start, leader);
+            if (valid) a.newpos[off + i] = start + __popc(m & lt);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+
+    // pass B: scatter into sorted order
+    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+        const int g = off + i;
+        const int q = off + a.newpos[g];
+        float4 xw = a.x_tmp[g];
+        X[q] = xw;
+        a.xref[q] = xw;
+        a.v[q] = a.v_tmp[g];
+        a.tag[q] = a.tag_tmp[g];
+        a.oldidx[q] = i;
+        a.bin_of[q] = a.binid[g];
+    }
+    if (kg) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
+            const int q = off + i;
+            int4 pr = a.partner_tmp[off + a.oldidx[q]];
+            int4 out;
+            out.x = pr.x >= 0 ? a.newpos[off + pr.x] : -1;
+            out.y = pr.y >= 0 ? a.newpos[off + pr.y] : -1;
+            out.z = pr.z >= 0 ? a.newpos[off + pr.z] : -1;
+            out.w = pr.w >= 0 ? a.newpos[off + pr.w] : -1;
+            a.partner[q] = out;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur) {
+    const int t = blockIdx.x;
+    const int c = a.tile_cell[t];
+    if (!a.built[c]) return;
+    __shared__ float s_H[8];
+    __shared__ float3 s_shift[27];
+    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
+    __syncthreads();
+
+    const int n = a.cell_n[c], off = a.cell_off[c];
+    const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
+    const float4 *X = cur ? a.x1 : a.x0;
+    int *nbr = a.nbr + (size_t)t * p.max_nb * RC_TILE + threadIdx.x;
+    int cnt = 0;
+    if (li < n) {
+        const int g = off + li;
+        const float4 xi = X[g];
+        const int nb0 = a.nbins[4 * c], nb1 = a.nbins[4 * c + 1], nb2 = a.nbins[4 * c + 2];
+        const int bin = a.bin_of[g];
+        const int b2 = bin % nb2, b1 = (bin / nb2) % nb1, b0 = bin / (nb1 * nb2);
+        const int *bs = a.bin_start + a.bin_off[c];
+        int4 pr = make_int4(-1, -1, -1, -1);
+        if (p.pot == RC_POT_KG) pr = a.partner[g];
+        for (int o0 = -1; o0 <= 1; o0++) {
+            int u0 = b0 + o0, s0 = u0 < 0 ? -1 : (u0 >= nb0 ? 1 : 0);
+            u0 -= s0 * nb0;
+            for (int o1 = -1; o1 <= 1; o1++) {
+                int u1 = b1 + o1, s1 = u1 < 0 ? -1 : (u1 >= nb1 ? 1 : 0);
+                u1 -= s1 * nb1;
+                for (int o2 = -1; o2 <= 1; o2++) {
+                    int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
+                    u2 -= s2 * nb2;
+                    const int code = (s0 + 1) + 3 * (s1 + 1) + 9 * (s2 + 1);
+                    const float3 sh = s_shift[code];
+                    const int bb = (u0 * nb1 + u1) * nb2 + u2;
+                    const int j0 = bs[bb], j1 = bs[bb + 1];
+                    const float bx = sh.x - xi.x, by = sh.y - xi.y, bz = sh.z - xi.z;
+                    for (int jl = j0; jl < j1; jl++) {
+                        if (jl == li && code == 13) continue;
+                        if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
+                        const float4 xj = X[off + jl];
+                        const float dx = xj.x + bx, dy = xj.y + by, dz = xj.z + bz;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < p.rlist2) {
+                            if (cnt < p.max_nb)
+                                nbr[(size_t)cnt * RC_TILE] = (int)((unsigned)(off + jl) | ((unsigned)code << RC_IDX_BITS));
+                            cnt++;
+                        }
+                    }
+                }
+            }
+        }
+        if (cnt > p.max_nb) {
+            rc_set_status(a.status, c, RC_EOVERFLOW);
+            cnt = p.max_nb;
+        }
+    }
+    a.nnb[off + li] = cnt;
+}
+
+}  // namespace
+
+void rc_launch_sort(const KParams &p, const KArrays &a, int cur, int n_cells, cudaStream_t s) {
+    k_sort<<<n_cells, SORT_THREADS, 0, s>>>(p, a, cur);
+}
+
+void rc_launch_nlist(const KParams &p, const KArrays &a, int cur, int n_tiles, cudaStream_t s) {
+    k_nlist<<<n_tiles, RC_TILE, 0, s>>>(p, a, cur);
+}

@@ -1,0 +1,143 @@
+// Internal definitions of the GB300 r-cell engine (not part of the C ABI).
+//
+// Data layout in HBM (one context = a batch of r-cells):
+//   * Atoms of all cells live in one padded array; cell c owns the slots
+//     [atom_off[c], atom_off[c] + ntile[c]*TILE), of which the first n[c] are
+//     real atoms.  A tile of TILE = 128 consecutive slots never spans two
+//     cells, so every CTA works for exactly one r-cell.
+//   * Positions: float4 {x, y, z, 0}, Cartesian in the cell's triangular MD box
+//     (ping-pong pair so one kernel can read x(t) of all neighbours while it
+//     writes x(t+dt) of its own atoms).  Velocities: float4 {vx, vy, vz, 0}.
+//   * Inside a cell, atoms are kept sorted by neighbour bin (counting sort at
+//     every list rebuild); `tag` maps a slot back to the caller's atom index.
+//   * Verlet list: per tile, column-major [TILE][max_nb] int32 entries
+//     j_global | (image << 27); the image code 0..26 selects one of the 27
+//     periodic shift vectors of the cell.
+//   * Per-cell FP64 state: box H, stretch R(t-1), Q, R, F of the last
+//     deformation, Philox force-evaluation counter, status word.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rcell.h"
+
+#define RC_TILE 128
+#define RC_IDX_BITS 27
+#define RC_IDX_MASK ((1u << RC_IDX_BITS) - 1u)
+#define RC_MAX_BONDS 4
+#define RC_MAX_BINS_PER_CELL 4096
+#define RC_SAMPLE_W 14  // per-step sample record: K[6], W[6], pe, ke
+
+// per-step force-kernel modes
+enum { MODE_EVAL = 0, MODE_SETUP = 1, MODE_STEP = 2, MODE_LAST = 3 };
+
+// Everything a kernel needs, passed by value.
+struct KParams {
+    int pot;
+    int units;
+    float eps, sigma, rc2, rlist2, skin_half2, skin2;
+    float sc_n, sc_m, sc_c;
+    float k_fene, R02, wca2;
+    float dt, fm;         // fm = (force -> acceleration) / mass
+    float inv_tau;        // 0 when the thermostat is off
+    float noise;          // sqrt(2 kT fm_units / (m tau dt))
+    float mvv2e;          // m v^2 -> energy units, times mass (per atom)
+    uint64_t seed;
+    int max_nb;
+};
+
+struct KArrays {
+    // per cell
+    const int *cell_n, *cell_off, *tile_cell, *cell_tile0;
+    const float *Hf;     // 8 floats per cell: h00 h01 h02 h11 h12 h22 . .
+    const float *Hif;    // inverse, same layout
+    const int *nbins;    // 4 ints per cell
+    const int *bin_off;  // first bin slot per cell
+    int *bin_start;      // bin_off[c] .. + nbins+1
+    int *status;
+    int *need_rebuild, *built;
+    const unsigned long long *evals;
+    double *series;      // [cell][slot][RC_SAMPLE_W]
+    int series_cap;
+    double *eval_acc;    // [cell][8]: pe, W xx yy zz xy xz yz, pad
+    // per atom
+    float4 *x0, *x1;     // ping-pong
+    float4 *v, *xref, *xr, *f;
+    int *tag;
+    int4 *partner;       // cell-local indices, -1 = none
+    int *nbr, *nnb, *bin_of;
+    // sort scratch
+    float4 *x_tmp, *v_tmp;
+    int *tag_tmp, *newpos, *oldidx, *binid;
+    int4 *partner_tmp;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), from the published round
+// definition: words (c0..c3), key (k0,k1); per round
+//   (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,
+//   c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0), then key += (W0, W1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 rc_philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        unsigned int hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned int hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Three standard normals for (tag, cell, force evaluation, seed): uniforms
+// u = (k + 1/2) 2^-32 and two Box-Muller pairs, of which three values are used.
+__device__ __forceinline__ float3 rc_normals3(unsigned int tag, unsigned int cell, unsigned long long ev,
+                                              unsigned long long seed) {
+    uint4 o = rc_philox(make_uint4(tag, cell, (unsigned int)ev, (unsigned int)(ev >> 32)),
+                        make_uint2((unsigned int)seed, (unsigned int)(seed >> 32)));
+    const float s = 2.3283064365386963e-10f, h = 1.1641532182693481e-10f;
+    float u0 = fmaf((float)o.x, s, h), u1 = fmaf((float)o.y, s, h);
+    float u2 = fmaf((float)o.z, s, h), u3 = fmaf((float)o.w, s, h);
+    float r0 = sqrtf(-2.0f * logf(u0)), r1 = sqrtf(-2.0f * logf(u2));
+    float s0, c0, s1, c1;
+    sincospif(2.0f * u1, &s0, &c0);
+    sincospif(2.0f * u3, &s1, &c1);
+    return make_float3(r0 * c0, r0 * s0, r1 * c1);
+}
+
+__device__ __forceinline__ void rc_set_status(int *status, int cell, int code) { atomicCAS(&status[cell], 0, code); }
+
+// Cartesian shift H * (sx, sy, sz) for image code 0..26 (code = (sx+1) + 3(sy+1) + 9(sz+1)),
+// H upper triangular {h00 h01 h02 h11 h12 h22}.
+__device__ __forceinline__ float3 rc_shift(const float *H, int code) {
+    float sx = (float)(code % 3 - 1), sy = (float)((code / 3) % 3 - 1), sz = (float)(code / 9 - 1);
+    return make_float3(H[0] * sx + H[1] * sy + H[2] * sz, H[3] * sy + H[4] * sz, H[5] * sz);
+}
+
+// host-side launchers (defined in the kernel translation units)
+void rc_launch_sort(const KParams &p, const KArrays &a, int cur, int n_cells, cudaStream_t s);
+void rc_launch_nlist(const KParams &p, const KArrays &a, int cur, int n_tiles, cudaStream_t s);
+void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s);
+void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
+                     int step_index, cudaStream_t s);
+void rc_launch_deform_impl(const double *F, double *H, double *Rprev, double *Q, double *R, double *Fst, double *dR,
+                           const double *H0, float *Hf, float *Hif, int *status, int *need_rebuild, int *nbins,
+                           const int *bin_cap, double rlist, int n_cells, cudaStream_t s);
+void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, cudaStream_t s);
+void rc_launch_stress(const double *series, int n_avg, int series_cap, const double *H, const double *Q,
+                      const double *F, double pconv, const int *status, double *sig_fem, double *sig_se,
+                      double *sig_md, double *P, int n_cells, cudaStream_t s);
+void rc_launch_advance(unsigned long long *evals, int n_cells, int n, cudaStream_t s);
+
+// finite elements (k_fe.cu)
+void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
+                        double *mass, int *err, cudaStream_t s);
+void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
+                        cudaStream_t s);
+void fe_launch_F(const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s);
+void fe_launch_fint(const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
+                    const double *d, double hg, double *fint, int ne, cudaStream_t s);
+void fe_launch_update(const int *mask, const double *mass, const double *fint, double dt, double damping,
+                      double *d, double *v, int n3, cudaStream_t s);
