@@ -35,12 +35,9 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0) return;
-    __shared__ float3 s_shift[27];
+    __shared__ ShiftTab s_tab;
     __shared__ float s_H[8];
-    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
-    __syncthreads();
+    rc_load_shifts(s_tab, s_H, a.Hf, c);
 
     const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
     const int n = a.cell_n[c], off = a.cell_off[c];
@@ -58,8 +55,8 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
         for (int k = sub; k < nn; k += TPA) {
             const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
             const float4 xj = __ldg(X + (e & RC_IDX_MASK));
-            const float3 sh = s_shift[e >> RC_IDX_BITS];
-            const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+            const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
+            const float dx = d.x, dy = d.y, dz = d.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (r2 < p.rc2) {
                 const float ar2 = a2 * __fdividef(1.0f, r2);
@@ -99,12 +96,9 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0) return;
-    __shared__ float3 s_shift[27];
+    __shared__ ShiftTab s_tab;
     __shared__ float s_H[8];
-    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
-    __syncthreads();
+    rc_load_shifts(s_tab, s_H, a.Hf, c);
 
     const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
     const int n = a.cell_n[c], off = a.cell_off[c];
@@ -128,8 +122,8 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
             for (int k = sub; k < nn; k += TPA) {
                 const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
                 const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
-                const float3 sh = s_shift[e >> RC_IDX_BITS];
-                const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+                const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
+                const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (r2 < p.rc2) {
                     const float ir2 = __fdividef(1.0f, r2);
@@ -163,8 +157,8 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
             for (int k = sub; k < nn; k += TPA) {
                 const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
                 const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
-                const float3 sh = s_shift[e >> RC_IDX_BITS];
-                const float dx = xj.x + sh.x - xi.x, dy = xj.y + sh.y - xi.y, dz = xj.z + sh.z - xi.z;
+                const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
+                const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (r2 < p.rc2) {
                     const float ir2 = __fdividef(1.0f, r2);
@@ -211,15 +205,17 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
         for (int b = 0; b < RC_MAX_BONDS; b++) {
             if (q[b] < 0) continue;
             const float4 xj = X[off + q[b]];
-            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            // minimum image through fractional coordinates
-            float s2_ = Hi[5] * dz, s1_ = Hi[3] * dy + Hi[4] * dz, s0_ = Hi[0] * dx + Hi[1] * dy + Hi[2] * dz;
-            s0_ = rintf(s0_);
-            s1_ = rintf(s1_);
-            s2_ = rintf(s2_);
-            dx -= s_H[0] * s0_ + s_H[1] * s1_ + s_H[2] * s2_;
-            dy -= s_H[3] * s1_ + s_H[4] * s2_;
-            dz -= s_H[5] * s2_;
+            // minimum image: pick the integer shift from fractional coordinates, then
+            // form the displacement through the exact shift table
+            const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
+            const float f2 = Hi[5] * ez, f1 = Hi[3] * ey + Hi[4] * ez, f0 = Hi[0] * ex + Hi[1] * ey + Hi[2] * ez;
+            const int n0 = -(int)rintf(f0), n1 = -(int)rintf(f1), n2 = -(int)rintf(f2);
+            if (n0 < -1 || n0 > 1 || n1 < -1 || n1 > 1 || n2 < -1 || n2 > 1) {
+                rc_set_status(a.status, c, RC_EBOND);
+                continue;
+            }
+            const float3 dd = rc_disp(xi, xj, s_tab, (n0 + 1) + 3 * (n1 + 1) + 9 * (n2 + 1));
+            const float dx = dd.x, dy = dd.y, dz = dd.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (!(r2 < p.R02)) {
                 rc_set_status(a.status, c, RC_EBOND);

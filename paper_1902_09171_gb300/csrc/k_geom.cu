@@ -57,6 +57,9 @@ __global__ void k_deform(const double *__restrict__ Fin, double *H, double *Rpre
             for (int k = i; k <= j; k++) s += R[3 * i + k] * h0[3 * k + j];
             Hn[3 * i + j] = s;
         }
+    // the MD box is held FP32-exact (positions are FP32): round it once here and
+    // use the rounded box everywhere (shifts, bins, volume)
+    for (int k = 0; k < 9; k++) Hn[k] = (double)(float)Hn[k];
     // perpendicular widths of an upper-triangular box [[a b c][0 d e][0 0 f]]:
     // w_d = 1 / |row d of H^{-1}|
     const double a = Hn[0], b = Hn[1], cc = Hn[2], d = Hn[4], e = Hn[5], f = Hn[8];
@@ -125,72 +128,97 @@ __global__ void k_remap(KArrays a, const double *__restrict__ dR, int cur) {
                        (float)(m[6] * x0 + m[7] * x1 + m[8] * x2), 0.0f);
 }
 
-// Mean and blocking standard error of component `comp` of the FE-frame stress
-// series of one cell; thread k < 6 handles component k.  Sample record:
-// K[6], W[6], pe, ke (raw sums); sigma_MD(t) = -(K + W) * pconv / det H.
-__device__ double sample_component(const double *rec, const double *Q, double scale, int comp) {
-    // symmetric MD-frame tensor
-    double S[9];
+// sigma_MD(t) = -(K + W) * pconv / det H from one sample record (K[6], W[6], pe, ke)
+__device__ __forceinline__ void sample_md(const double *rec, double scale, double *S /* 9 */) {
     const int vi[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
     for (int k = 0; k < 6; k++) {
         const double s = -(rec[k] + rec[6 + k]) * scale;
         S[3 * vi[k][0] + vi[k][1]] = s;
         S[3 * vi[k][1] + vi[k][0]] = s;
     }
-    if (!Q) return S[3 * vi[comp][0] + vi[comp][1]];
-    const int a = vi[comp][0], b = vi[comp][1];
-    double r = 0.0;
-    for (int k = 0; k < 3; k++)
-        for (int l = 0; l < 3; l++) r += Q[3 * a + k] * S[3 * k + l] * Q[3 * b + l];
-    return r;
 }
 
-__global__ void k_stress(const double *__restrict__ series, int n_avg, int cap, const double *__restrict__ H,
-                         const double *__restrict__ Qall, const double *__restrict__ Fall, double pconv,
-                         const int *status, double *sig_fem, double *sig_se, double *sig_md, double *P) {
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// One CTA per cell.  Phase 1: every sample rotated to the FE frame
+// (Q sigma_MD Q^T) into `rot` (n_avg x 6).  Phase 2: warp k < 6 takes component
+// k: mean and the blocking standard error (level l: floor(n/2^l) block means;
+// largest SE over levels with >= 16 blocks, level 0 always).  Phase 3: P.
+constexpr int STRESS_THREADS = 256;
+__global__ void __launch_bounds__(STRESS_THREADS) k_stress(const double *__restrict__ series, int n_avg, int cap,
+                         const double *__restrict__ H, const double *__restrict__ Qall,
+                         const double *__restrict__ Fall, double pconv, double *rot_all, double *sig_fem,
+                         double *sig_se, double *sig_md, double *P) {
     const int c = blockIdx.x;
-    const int k = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double s_md[STRESS_THREADS / 32][6];
     __shared__ double s_mean[6];
     const double *Hc = H + 9 * c, *Q = Qall + 9 * c;
-    const double V = Hc[0] * Hc[4] * Hc[8];
-    const double scale = pconv / V;
+    const double scale = pconv / (Hc[0] * Hc[4] * Hc[8]);
     const double *rec0 = series + (size_t)c * cap * RC_SAMPLE_W;
-    if (k < 6) {
-        double sum = 0.0, sum_md = 0.0;
-        for (int t = 0; t < n_avg; t++) {
-            sum += sample_component(rec0 + (size_t)t * RC_SAMPLE_W, Q, scale, k);
-            sum_md += sample_component(rec0 + (size_t)t * RC_SAMPLE_W, nullptr, scale, k);
+    double *rot = rot_all + (size_t)c * cap * 6;
+    const int vi[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    double md[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = tid; t < n_avg; t += STRESS_THREADS) {
+        double S[9];
+        sample_md(rec0 + (size_t)t * RC_SAMPLE_W, scale, S);
+        for (int k = 0; k < 6; k++) {
+            const int a = vi[k][0], b = vi[k][1];
+            double r = 0.0;
+            for (int u = 0; u < 3; u++)
+                for (int v = 0; v < 3; v++) r += Q[3 * a + u] * S[3 * u + v] * Q[3 * b + v];
+            rot[(size_t)t * 6 + k] = r;
+            md[k] += S[3 * a + b];
         }
+    }
+    for (int k = 0; k < 6; k++) {
+        const double w = warp_sum(md[k]);
+        if (lane == 0) s_md[warp][k] = w;
+    }
+    __syncthreads();
+    if (warp < 6) {
+        const int k = warp;
+        double sum = 0.0;
+        for (int t = lane; t < n_avg; t += 32) sum += rot[(size_t)t * 6 + k];
+        sum = warp_sum(sum);
         const double mean = n_avg > 0 ? sum / n_avg : 0.0;
         double best = 0.0;
         for (int lvl = 0;; lvl++) {
             const int bs = 1 << lvl, nk = n_avg / bs;
-            if (nk < 2) break;
-            if (lvl > 0 && nk < 16) break;
+            if (nk < 2 || (lvl > 0 && nk < 16)) break;
             double mb = 0.0;
-            for (int b = 0; b < nk; b++) {
+            for (int b = lane; b < nk; b += 32) {
                 double m = 0.0;
-                for (int t = 0; t < bs; t++) m += sample_component(rec0 + (size_t)(b * bs + t) * RC_SAMPLE_W, Q, scale, k);
+                for (int t = 0; t < bs; t++) m += rot[(size_t)(b * bs + t) * 6 + k];
                 mb += m / bs;
             }
-            mb /= nk;
+            mb = warp_sum(mb) / nk;
             double v = 0.0;
-            for (int b = 0; b < nk; b++) {
+            for (int b = lane; b < nk; b += 32) {
                 double m = 0.0;
-                for (int t = 0; t < bs; t++) m += sample_component(rec0 + (size_t)(b * bs + t) * RC_SAMPLE_W, Q, scale, k);
+                for (int t = 0; t < bs; t++) m += rot[(size_t)(b * bs + t) * 6 + k];
                 m /= bs;
                 v += (m - mb) * (m - mb);
             }
+            v = warp_sum(v);
             const double se = sqrt(v / ((double)nk * (nk - 1)));
             if (se > best) best = se;
         }
-        sig_fem[6 * c + k] = mean;
-        sig_se[6 * c + k] = best;
-        sig_md[6 * c + k] = n_avg > 0 ? sum_md / n_avg : 0.0;
-        s_mean[k] = mean;
+        if (lane == 0) {
+            double mdsum = 0.0;
+            for (int w = 0; w < STRESS_THREADS / 32; w++) mdsum += s_md[w][k];
+            sig_fem[6 * c + k] = mean;
+            sig_se[6 * c + k] = best;
+            sig_md[6 * c + k] = n_avg > 0 ? mdsum / n_avg : 0.0;
+            s_mean[k] = mean;
+        }
     }
     __syncthreads();
-    if (k == 0) {
+    if (tid == 0) {
         // P = J sigma F^{-T}
         const double *F = Fall + 9 * c;
         const double J = det3(F);
@@ -234,9 +262,10 @@ void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, c
 }
 
 void rc_launch_stress(const double *series, int n_avg, int series_cap, const double *H, const double *Q,
-                      const double *F, double pconv, const int *status, double *sig_fem, double *sig_se,
+                      const double *F, double pconv, double *rot_scratch, double *sig_fem, double *sig_se,
                       double *sig_md, double *P, int n_cells, cudaStream_t s) {
-    k_stress<<<n_cells, 32, 0, s>>>(series, n_avg, series_cap, H, Q, F, pconv, status, sig_fem, sig_se, sig_md, P);
+    k_stress<<<n_cells, STRESS_THREADS, 0, s>>>(series, n_avg, series_cap, H, Q, F, pconv, rot_scratch, sig_fem,
+                                                sig_se, sig_md, P);
 }
 
 void rc_launch_advance(unsigned long long *evals, int n_cells, int n, cudaStream_t s) {

@@ -166,11 +166,8 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
     const int c = a.tile_cell[t];
     if (!a.built[c]) return;
     __shared__ float s_H[8];
-    __shared__ float3 s_shift[27];
-    if (threadIdx.x < 6) s_H[threadIdx.x] = a.Hf[8 * c + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < 27) s_shift[threadIdx.x] = rc_shift(s_H, threadIdx.x);
-    __syncthreads();
+    __shared__ ShiftTab s_tab;
+    rc_load_shifts(s_tab, s_H, a.Hf, c);
 
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
@@ -196,16 +193,14 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                     int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
                     u2 -= s2 * nb2;
                     const int code = (s0 + 1) + 3 * (s1 + 1) + 9 * (s2 + 1);
-                    const float3 sh = s_shift[code];
                     const int bb = (u0 * nb1 + u1) * nb2 + u2;
                     const int j0 = bs[bb], j1 = bs[bb + 1];
-                    const float bx = sh.x - xi.x, by = sh.y - xi.y, bz = sh.z - xi.z;
                     for (int jl = j0; jl < j1; jl++) {
                         if (jl == li && code == 13) continue;
                         if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
                         const float4 xj = X[off + jl];
-                        const float dx = xj.x + bx, dy = xj.y + by, dz = xj.z + bz;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float3 d = rc_disp(xi, xj, s_tab, code);
+                        const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
                         if (r2 < p.rlist2) {
                             if (cnt < p.max_nb)
                                 nbr[(size_t)cnt * RC_TILE] = (int)((unsigned)(off + jl) | ((unsigned)code << RC_IDX_BITS));

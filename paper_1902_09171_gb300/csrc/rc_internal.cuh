@@ -109,11 +109,42 @@ __device__ __forceinline__ float3 rc_normals3(unsigned int tag, unsigned int cel
 
 __device__ __forceinline__ void rc_set_status(int *status, int cell, int code) { atomicCAS(&status[cell], 0, code); }
 
-// Cartesian shift H * (sx, sy, sz) for image code 0..26 (code = (sx+1) + 3(sy+1) + 9(sz+1)),
-// H upper triangular {h00 h01 h02 h11 h12 h22}.
-__device__ __forceinline__ float3 rc_shift(const float *H, int code) {
-    float sx = (float)(code % 3 - 1), sy = (float)((code / 3) % 3 - 1), sz = (float)(code / 9 - 1);
-    return make_float3(H[0] * sx + H[1] * sy + H[2] * sz, H[3] * sy + H[4] * sz, H[5] * sz);
+// Periodic image shift tables.  The MD box H is stored FP32-exact (the FP64
+// box of the deformation is rounded once), so the Cartesian shift
+// sh = H (sx, sy, sz) of image code (sx+1) + 3(sy+1) + 9(sz+1) is exact in FP64
+// and split into an FP32 value plus an FP32 remainder `lo` (nonzero only for
+// combinations of tilted box vectors).  The displacement x_j + sh - x_i is then
+// formed as ((x_j + sn) - (x_i - sp)) + lo with sn = min(sh, 0), sp = max(sh, 0):
+// x_j + sn and x_i - sp subtract numbers of similar size (exact), so only the
+// final subtraction rounds -- the result is the correctly rounded displacement
+// instead of one carrying an error of half an ulp of the box length.
+struct ShiftTab {
+    float4 sn[27], sp[27], lo[27];
+};
+
+__device__ __forceinline__ void rc_build_shift(ShiftTab &T, const float *H, int code) {
+    const double sx = (double)(code % 3 - 1), sy = (double)((code / 3) % 3 - 1), sz = (double)(code / 9 - 1);
+    const double hx = (double)H[0] * sx + (double)H[1] * sy + (double)H[2] * sz;
+    const double hy = (double)H[3] * sy + (double)H[4] * sz;
+    const double hz = (double)H[5] * sz;
+    const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
+    T.sn[code] = make_float4(fminf(fx, 0.f), fminf(fy, 0.f), fminf(fz, 0.f), 0.f);
+    T.sp[code] = make_float4(fmaxf(fx, 0.f), fmaxf(fy, 0.f), fmaxf(fz, 0.f), 0.f);
+    T.lo[code] = make_float4((float)(hx - fx), (float)(hy - fy), (float)(hz - fz), 0.f);
+}
+
+// fill the table from cell c's box (call with all threads; syncs)
+__device__ __forceinline__ void rc_load_shifts(ShiftTab &T, float *s_H, const float *Hf, int c) {
+    if (threadIdx.x < 6) s_H[threadIdx.x] = Hf[8 * c + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < 27) rc_build_shift(T, s_H, threadIdx.x);
+    __syncthreads();
+}
+
+__device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, const ShiftTab &T, int code) {
+    const float4 sn = T.sn[code], sp = T.sp[code], lo = T.lo[code];
+    return make_float3(((xj.x + sn.x) - (xi.x - sp.x)) + lo.x, ((xj.y + sn.y) - (xi.y - sp.y)) + lo.y,
+                       ((xj.z + sn.z) - (xi.z - sp.z)) + lo.z);
 }
 
 // host-side launchers (defined in the kernel translation units)
@@ -127,7 +158,7 @@ void rc_launch_deform_impl(const double *F, double *H, double *Rprev, double *Q,
                            const int *bin_cap, double rlist, int n_cells, cudaStream_t s);
 void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, cudaStream_t s);
 void rc_launch_stress(const double *series, int n_avg, int series_cap, const double *H, const double *Q,
-                      const double *F, double pconv, const int *status, double *sig_fem, double *sig_se,
+                      const double *F, double pconv, double *rot_scratch, double *sig_fem, double *sig_se,
                       double *sig_md, double *P, int n_cells, cudaStream_t s);
 void rc_launch_advance(unsigned long long *evals, int n_cells, int n, cudaStream_t s);
 

@@ -41,6 +41,7 @@ struct rcell_ctx {
     int *d_nbins = nullptr, *d_bin_cap = nullptr;
     unsigned long long *d_evals = nullptr;
     double *d_sig_fem = nullptr, *d_sig_se = nullptr, *d_sig_md = nullptr, *d_P = nullptr;
+    double *d_rot = nullptr;  // stress reduction scratch, n_cells x series_cap x 6
     int series_cap = 0;
     int last_n_avg = -1;
     int cur = 0;
@@ -142,13 +143,18 @@ int ensure_series(rcell_ctx *c, int n_avg) {
     int cap = std::max(n_avg, 256);
     double *p = nullptr;
     CKC(c, cudaStreamSynchronize(c->stream));
+    double *rot = nullptr;
     CKC(c, cudaMalloc(&p, sizeof(double) * (size_t)c->n_cells * cap * RC_SAMPLE_W));
-    if (c->ka.series) {
-        auto it = std::find(c->allocs.begin(), c->allocs.end(), (void *)c->ka.series);
+    CKC(c, cudaMalloc(&rot, sizeof(double) * (size_t)c->n_cells * cap * 6));
+    for (void *old : {(void *)c->ka.series, (void *)c->d_rot}) {
+        if (!old) continue;
+        auto it = std::find(c->allocs.begin(), c->allocs.end(), old);
         if (it != c->allocs.end()) c->allocs.erase(it);
-        cudaFree(c->ka.series);
+        cudaFree(old);
     }
     c->allocs.push_back(p);
+    c->allocs.push_back(rot);
+    c->d_rot = rot;
     c->ka.series = p;
     c->ka.series_cap = cap;
     c->series_cap = cap;
@@ -418,7 +424,7 @@ int rcell_stress(rcell_ctx *c, double *sigma, double *sigma_stderr, double *P, i
     if (!c) return RC_EINVAL;
     if (c->last_n_avg <= 0) return fail(c, RC_ESTATE, "no stress samples: run with n_avg > 0 first");
     rc_launch_stress(c->ka.series, c->last_n_avg, c->series_cap, c->d_H, c->d_Q, c->d_F, pconv_of(c->prm.units),
-                     c->ka.status, c->d_sig_fem, c->d_sig_se, c->d_sig_md, c->d_P, c->n_cells, c->stream);
+                     c->d_rot, c->d_sig_fem, c->d_sig_se, c->d_sig_md, c->d_P, c->n_cells, c->stream);
     CKC(c, cudaGetLastError());
     const cudaMemcpyKind kind = where == RC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const size_t n6 = sizeof(double) * 6 * c->n_cells, n9 = sizeof(double) * 9 * c->n_cells;
@@ -682,7 +688,7 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
     if (c->last_n_avg > 0) {
         CKC(c, cudaEventRecord(ev[0], c->stream));
         rc_launch_stress(c->ka.series, c->last_n_avg, c->series_cap, c->d_H, c->d_Q, c->d_F, pconv_of(c->prm.units),
-                         c->ka.status, c->d_sig_fem, c->d_sig_se, c->d_sig_md, c->d_P, c->n_cells, c->stream);
+                         c->d_rot, c->d_sig_fem, c->d_sig_se, c->d_sig_md, c->d_P, c->n_cells, c->stream);
         CKC(c, cudaEventRecord(ev[1], c->stream));
         CKC(c, cudaEventSynchronize(ev[1]));
         lap(0, 1, 6);
