@@ -354,7 +354,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--md-steps", type=int, default=MD_STEPS)
-    ap.add_argument("--skin", type=float, default=0.5)
+    ap.add_argument("--skin", type=float, default=1.5)
     ap.add_argument("--tpa", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -331,7 +331,7 @@ def params_lj_cu(tau=0.1, kT=None, dt=0.002, seed=1, skin=0.5):
                         tau, dt, seed)
 
 
-def params_sc_cu(tau=0.1, kT=None, dt=0.002, seed=1, skin=0.5):
+def params_sc_cu(tau=0.1, kT=None, dt=0.002, seed=1, skin=1.5):
     """Sutton-Chen copper: n = 9, m = 6, eps = 1.2382e-2 eV, c = 39.432, a = 3.61 A, rc = 2a."""
     kT = 300 * 8.617333262e-5 if kT is None else kT
     return rcell_params(RC_POT_SC, RC_UNITS_METAL, 1.2382e-2, 3.61, 7.22, 9.0, 6.0, 39.432, 0, 0, skin, 63.546,
