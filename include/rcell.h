@@ -201,6 +201,26 @@ int rcell_profile_kernels(rcell_ctx *ctx, int n_steps, double *ms_out);
 int rcell_checkpoint(rcell_ctx *ctx, int cell, void *buf, size_t *bytes);
 int rcell_restore(rcell_ctx *ctx, int cell, const void *buf, size_t bytes);
 
+/* Allocation-free stress reduction, for callers that cannot allocate device
+ * memory when they need the stress (inside a stream capture under the global
+ * capture mode, from a stream callback, or under a fixed up-front memory
+ * budget).  The paper has no counterpart: it is the reduction of rcell_stress
+ * taken out of the context, with its scratch in a fixed device array of the
+ * library instead of memory the context allocated.
+ *   series       device, n_cells x n_avg x 6: MD-frame tension-positive stress
+ *                samples (Voigt), e.g. what rcell_get_series returns
+ *   Q, F         device, n_cells x 9 each: rotation and deformation gradient
+ *   sigma        device, n_cells x 6: mean of Q sigma(t) Q^T (required)
+ *   sigma_stderr device, n_cells x 6 or NULL: blocking standard error
+ *   P            device, n_cells x 9 or NULL: J sigma F^{-T}
+ *   stream       cudaStream_t to enqueue on (NULL = default stream)
+ * n_cells * n_avg must not exceed 65536 (RC_EINVAL otherwise, nothing runs).
+ * Allocates nothing.  All calls share the scratch array: calls whose kernels
+ * overlap on the GPU race.  The first call on a device looks the array up
+ * (device current); make it before any stream capture.  Asynchronous. */
+int rcell_stress_reduce_static(const double *series, int n_cells, int n_avg, const double *Q, const double *F,
+                               double *sigma, double *sigma_stderr, double *P, void *stream);
+
 /* One-line description of the last error on this context (never NULL). */
 const char *rcell_last_error(const rcell_ctx *ctx);
 

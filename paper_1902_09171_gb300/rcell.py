@@ -47,7 +47,7 @@ _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
            "rcell_clear_status", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
-           "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step",
+           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step",
            "fe_get_state", "fe_destroy"]
 
 
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
         "rcell_checkpoint": ([vp, C.c_int, vp, C.POINTER(C.c_size_t)], C.c_int),
         "rcell_restore": ([vp, C.c_int, vp, C.c_size_t], C.c_int),
+        "rcell_stress_reduce_static": ([vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
         "rcell_last_error": ([vp], C.c_char_p),
         "rcell_destroy": ([vp], None),
         "fe_create": ([vp, C.c_int, vp, C.c_int, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp,
@@ -267,6 +268,15 @@ def rcell_checkpoint(ctx, cell: int) -> bytes:
 def rcell_restore(ctx, cell: int, blob: bytes):
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().rcell_restore(ctx, cell, buf, len(blob)), ctx, "rcell_restore")
+
+
+def rcell_stress_reduce_static(series, Q, F, sigma, sigma_stderr=None, P=None, stream=None):
+    """Allocation-free stress reduction; all arrays are CUDA tensors (float64).
+    series: (n_cells, n_avg, 6); Q, F: (n_cells, 3, 3); outputs preallocated."""
+    n_cells, n_avg = int(series.shape[0]), int(series.shape[1])
+    ptr = [None if a is None else C.c_void_p(a.data_ptr()) for a in (series, Q, F, sigma, sigma_stderr, P)]
+    _check(load().rcell_stress_reduce_static(ptr[0], n_cells, n_avg, ptr[1], ptr[2], ptr[3], ptr[4], ptr[5],
+                                             _stream_ptr(stream)), None, "rcell_stress_reduce_static")
 
 
 def rcell_last_error(ctx) -> str:
