@@ -28,6 +28,34 @@ __device__ __forceinline__ float sub_sum(float v) {
     return v;
 }
 
+// Walk one atom's Verlet list (this lane's share: entries sub, sub+TPA, ...),
+// U entries at a time: the U list words are loaded first, then the U neighbour
+// positions, then the U pair evaluations run -- U independent memory requests in
+// flight per thread instead of one.  fn(xj, d) receives the neighbour's record
+// and the exact periodic displacement d = x_j(image) - x_i.
+constexpr int RC_UNROLL = 4;
+template <int TPA, class Fn>
+__device__ __forceinline__ void for_each_neighbor(const int *__restrict__ nb, int nn, int sub,
+                                                  const float4 *__restrict__ XG, const float4 &xi, const ShiftTab &T,
+                                                  Fn &&fn) {
+    int k = sub;
+    for (; k + (RC_UNROLL - 1) * TPA < nn; k += RC_UNROLL * TPA) {
+        unsigned e[RC_UNROLL];
+        float4 xj[RC_UNROLL];
+#pragma unroll
+        for (int u = 0; u < RC_UNROLL; u++) e[u] = (unsigned)__ldg(nb + (size_t)(k + u * TPA) * RC_TILE);
+#pragma unroll
+        for (int u = 0; u < RC_UNROLL; u++) xj[u] = __ldg(XG + (e[u] & RC_IDX_MASK));
+#pragma unroll
+        for (int u = 0; u < RC_UNROLL; u++) fn(xj[u], rc_disp(xi, xj[u], T, e[u] >> RC_IDX_BITS));
+    }
+    for (; k < nn; k += TPA) {
+        const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
+        const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
+        fn(xj, rc_disp(xi, xj, T, e >> RC_IDX_BITS));
+    }
+}
+
 // Sutton-Chen density pass: rho_i = sum_j (a/r_ij)^m over r < rc; writes
 // xr_i = {x_i, rho_i^{-1/2}} for the force pass.
 template <int TPA, bool M6>
@@ -52,17 +80,14 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
         const int nn = a.nnb[g];
         const int *__restrict__ nb = a.nbr + (size_t)t * p.max_nb * RC_TILE + at;
         const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m;
-        for (int k = sub; k < nn; k += TPA) {
-            const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
-            const float4 xj = __ldg(X + (e & RC_IDX_MASK));
-            const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
-            const float dx = d.x, dy = d.y, dz = d.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < p.rc2) {
+        const float rc2 = p.rc2;
+        for_each_neighbor<TPA>(nb, nn, sub, X, xi, s_tab, [&](const float4 &, const float3 &d) {
+            const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+            if (r2 < rc2) {
                 const float ar2 = a2 * __fdividef(1.0f, r2);
                 rho += M6 ? ar2 * ar2 * ar2 : powf(ar2, hm);
             }
-        }
+        });
     }
     rho = sub_sum<TPA>(rho);
     if (live && sub == 0) a.xr[g] = make_float4(xi.x, xi.y, xi.z, rho > 0.0f ? rsqrtf(rho) : 0.0f);
@@ -119,25 +144,23 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
         if (POT == RC_POT_SC) {
             const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m, hn = 0.5f * p.sc_n;
             const float cm2 = 0.5f * p.sc_c * p.sc_m;
-            for (int k = sub; k < nn; k += TPA) {
-                const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
-                const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
-                const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
+            const float rc2 = p.rc2, eps = p.eps, sc_n = p.sc_n, sig = p.sigma;
+            for_each_neighbor<TPA>(nb, nn, sub, XG, xi, s_tab, [&](const float4 &xj, const float3 &d) {
                 const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < p.rc2) {
+                if (r2 < rc2) {
                     const float ir2 = __fdividef(1.0f, r2);
                     const float ar2 = a2 * ir2;
                     float arm, arn;
                     if (M6) {
-                        arm = ar2 * ar2 * ar2;                     // (a/r)^6
-                        arn = arm * ar2 * (p.sigma * rsqrtf(r2));  // (a/r)^9
+                        arm = ar2 * ar2 * ar2;               // (a/r)^6
+                        arn = arm * ar2 * (sig * rsqrtf(r2));  // (a/r)^9
                     } else {
                         arm = powf(ar2, hm);
                         arn = powf(ar2, hn);
                     }
                     // dE/dr / r = eps / r^2 [ -n (a/r)^n + c m/2 (rho_i^-1/2 + rho_j^-1/2) (a/r)^m ]
-                    const float gr = p.eps * ir2 * fmaf(cm2 * (xi.w + xj.w), arm, -p.sc_n * arn);
+                    const float gr = eps * ir2 * fmaf(cm2 * (xi.w + xj.w), arm, -sc_n * arn);
                     fx = fmaf(gr, dx, fx);
                     fy = fmaf(gr, dy, fy);
                     fz = fmaf(gr, dz, fz);
@@ -148,19 +171,17 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
                     w3 = fmaf(hx, dy, w3);
                     w4 = fmaf(hx, dz, w4);
                     w5 = fmaf(hy, dz, w5);
-                    pe = fmaf(0.5f * p.eps, arn, pe);
+                    pe = fmaf(0.5f * eps, arn, pe);
                 }
-            }
+            });
         } else {
             const float s2 = p.sigma * p.sigma;
             const float c24 = 24.0f * p.eps, c2 = 2.0f * p.eps;
-            for (int k = sub; k < nn; k += TPA) {
-                const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
-                const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
-                const float3 d = rc_disp(xi, xj, s_tab, e >> RC_IDX_BITS);
+            const float rc2 = p.rc2;
+            for_each_neighbor<TPA>(nb, nn, sub, XG, xi, s_tab, [&](const float4 &, const float3 &d) {
                 const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < p.rc2) {
+                if (r2 < rc2) {
                     const float ir2 = __fdividef(1.0f, r2);
                     const float sr2 = s2 * ir2;
                     const float sr6 = sr2 * sr2 * sr2;
@@ -178,7 +199,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
                     w5 = fmaf(hy, dz, w5);
                     pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
                 }
-            }
+            });
         }
     }
     fx = sub_sum<TPA>(fx);
