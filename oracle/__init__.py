@@ -4,7 +4,8 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product path (the CUDA library and
 its Python binding) never imports, links or executes anything here, and this
 package shares no code with it: the arithmetic lives in ``rcell_oracle.c``
-(plain C, FP64).
+(plain C, FP64) and, for the learned surrogate, in ``mlp.py`` (plain NumPy,
+FP64).
 
 The functions below are thin ctypes marshalling around the C routines; each C
 routine names the passage of the paper (or the potential / integrator
