@@ -1,0 +1,620 @@
+// Recurrent-MLP stress surrogate on tensor cores: BF16 operands, FP32
+// accumulation (mma.sync m16n8k16), fused epilogues, BPTT and AdamW.
+//
+// GEMM: C[M x N] = op(A)[M x K] * B[K x N], op(A) = A (row-major, lda) or A^T
+// (A stored K x M).  CTA tile 64 x 64 x 32, four warps of 32 x 32; operand
+// tiles staged in shared memory (A as [m][k], B as [n][k], k contiguous, so
+// every fragment register is one aligned 32-bit shared load).  Epilogues fuse
+// bias + GELU (forward), the head (stress output + tanh state written straight
+// into the next step's input row), GELU' (backward) and split-K FP32 weight
+// gradient accumulation.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/surrogate.h"
+#include "rc_internal.cuh"
+
+namespace {
+
+constexpr int K0 = 144, WID = 256, N4 = 144, NIN = SUR_N_IN, NH = SUR_N_H, NOUT = SUR_N_OUT;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + K0 * WID, OFF_W2 = OFF_B1 + WID, OFF_B2 = OFF_W2 + WID * WID,
+              OFF_W3 = OFF_B2 + WID, OFF_B3 = OFF_W3 + WID * WID, OFF_W4 = OFF_B3 + WID, OFF_B4 = OFF_W4 + WID * N4,
+              NPAR = OFF_B4 + N4;
+static_assert(NPAR == SUR_N_PARAMS, "parameter layout");
+
+constexpr int BM = 64, BN = 64, BK = 32, PADK = 8, GEMM_THREADS = 128;
+
+enum { EPI_GELU = 0, EPI_HEAD = 1, EPI_DGELU = 2, EPI_F32 = 3, EPI_WGRAD = 4 };
+
+struct Epi {
+    const float *bias;       // GELU, HEAD
+    __nv_bfloat16 *y_out;    // GELU: pre-activation
+    __nv_bfloat16 *a_out;    // GELU: activation; DGELU: dy out
+    int ld_out;
+    const __nv_bfloat16 *y_in;  // DGELU: pre-activation
+    int ld_in;
+    float *s_out;            // HEAD: stress (row stride s_ld), F32/WGRAD: C
+    int s_ld;
+    __nv_bfloat16 *h_next;   // HEAD: next step's input row block (columns NIN..NIN+NH), may be null
+    float *h_f32;            // HEAD: FP32 copy of h (ld NH), may be null
+    const float *s_mul;      // HEAD: per-component stress scale (null: network units)
+};
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int EPI>
+__device__ __forceinline__ void epilogue(const Epi &e, int m, int n, int M, int N, float acc) {
+    if (m >= M || n >= N) return;
+    if (EPI == EPI_GELU) {
+        const float y = acc + e.bias[n];
+        e.y_out[(size_t)m * e.ld_out + n] = __float2bfloat16(y);
+        e.a_out[(size_t)m * e.ld_out + n] = __float2bfloat16(gelu_f(y));
+    } else if (EPI == EPI_HEAD) {
+        const float o = acc + e.bias[n];
+        if (n < NOUT) {
+            e.s_out[(size_t)m * e.s_ld + n] = e.s_mul ? o * e.s_mul[n] : o;
+        } else if (n < NOUT + NH) {
+            const float h = tanhf(o);
+            if (e.h_next) e.h_next[(size_t)m * K0 + NIN + (n - NOUT)] = __float2bfloat16(h);
+            if (e.h_f32) e.h_f32[(size_t)m * NH + (n - NOUT)] = h;
+        }
+    } else if (EPI == EPI_DGELU) {
+        const float y = __bfloat162float(e.y_in[(size_t)m * e.ld_in + n]);
+        e.a_out[(size_t)m * e.ld_out + n] = __float2bfloat16(acc * gelu_d(y));
+    } else if (EPI == EPI_F32) {
+        e.s_out[(size_t)m * e.s_ld + n] = acc;
+    } else {  // EPI_WGRAD: split-K partial sums
+        atomicAdd(&e.s_out[(size_t)m * e.s_ld + n], acc);
+    }
+}
+
+template <int EPI, bool TRANS_A>
+__global__ void __launch_bounds__(GEMM_THREADS) k_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                       const __nv_bfloat16 *__restrict__ B, int ldb, int M, int N,
+                                                       int K, int k_chunk, Epi e) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, q = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * k_chunk, ke = min(K, kb + k_chunk);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[i][j][r] = 0.f;
+    const uint4 zero4 = make_uint4(0, 0, 0, 0);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        // ---- stage op(A) tile [BM][BK] ----
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+            const int idx = tid + it * GEMM_THREADS;  // 256 chunks of 8 elements
+            if (!TRANS_A) {
+                const int r = idx >> 2, kc = (idx & 3) * 8;
+                uint4 v = zero4;
+                if (m0 + r < M && k0 + kc < ke) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + k0 + kc);
+                *reinterpret_cast<uint4 *>(&As[r][kc]) = v;
+            } else {
+                const int kr = idx >> 3, mc = (idx & 7) * 8;
+                uint4 v = zero4;
+                if (k0 + kr < ke && m0 + mc < M) v = *reinterpret_cast<const uint4 *>(A + (size_t)(k0 + kr) * lda + m0 + mc);
+                const __nv_bfloat16 *pv = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int i = 0; i < 8; i++) As[mc + i][kr] = pv[i];
+            }
+        }
+        // ---- stage B tile as [BN][BK] ----
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+            const int idx = tid + it * GEMM_THREADS;
+            const int kr = idx >> 3, nc = (idx & 7) * 8;
+            uint4 v = zero4;
+            if (k0 + kr < ke && n0 + nc < N) v = *reinterpret_cast<const uint4 *>(B + (size_t)(k0 + kr) * ldb + n0 + nc);
+            const __nv_bfloat16 *pv = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+            for (int i = 0; i < 8; i++) Bs[nc + i][kr] = pv[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++) {
+                const int r = wm * 32 + mi * 16 + g;
+                a[mi][0] = *reinterpret_cast<const unsigned *>(&As[r][kk + 2 * q]);
+                a[mi][1] = *reinterpret_cast<const unsigned *>(&As[r + 8][kk + 2 * q]);
+                a[mi][2] = *reinterpret_cast<const unsigned *>(&As[r][kk + 8 + 2 * q]);
+                a[mi][3] = *reinterpret_cast<const unsigned *>(&As[r + 8][kk + 8 + 2 * q]);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ni++) {
+                const int c = wn * 32 + ni * 8 + g;
+                b[ni][0] = *reinterpret_cast<const unsigned *>(&Bs[c][kk + 2 * q]);
+                b[ni][1] = *reinterpret_cast<const unsigned *>(&Bs[c][kk + 8 + 2 * q]);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) {
+            const int m = m0 + wm * 32 + mi * 16 + g, n = n0 + wn * 32 + ni * 8 + 2 * q;
+            epilogue<EPI>(e, m, n, M, N, acc[mi][ni][0]);
+            epilogue<EPI>(e, m, n + 1, M, N, acc[mi][ni][1]);
+            epilogue<EPI>(e, m + 8, n, M, N, acc[mi][ni][2]);
+            epilogue<EPI>(e, m + 8, n + 1, M, N, acc[mi][ni][3]);
+        }
+}
+
+template <int EPI, bool TRANS_A>
+void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K,
+          const Epi &e, int split_k = 1) {
+    int chunk = (K + split_k - 1) / split_k;
+    chunk = (chunk + BK - 1) / BK * BK;
+    const int nz = (K + chunk - 1) / chunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nz);
+    k_gemm<EPI, TRANS_A><<<grid, GEMM_THREADS, 0, s>>>(A, lda, B, ldb, M, N, K, chunk, e);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+
+// z_t rows: [u_t / u_scale, h_{t-1} (already there, or zero at t = 0), 0]
+__global__ void k_build_input(const float *__restrict__ U, int B, int T, int t, const float *__restrict__ u_inv,
+                              __nv_bfloat16 *Z, int zero_state) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * K0) return;
+    const int b = idx / K0, k = idx % K0;
+    if (k < NIN) Z[idx] = __float2bfloat16(U[((size_t)b * T + t) * NIN + k] * u_inv[k]);
+    else if (k >= NIN + NH || zero_state) Z[idx] = __float2bfloat16(0.0f);
+}
+
+// head gradient do_t = [scale (s - y/s_scale), dh (1 - h^2), 0]; loss partials
+__global__ void k_head_grad(const float *__restrict__ S, const float *__restrict__ Y, int B, int T, int t,
+                            const float *__restrict__ s_inv, const __nv_bfloat16 *__restrict__ Hrow,
+                            const float *__restrict__ dZ, int have_dh, float gscale, __nv_bfloat16 *dO,
+                            double *loss_acc) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (idx < B * N4) {
+        const int b = idx / N4, n = idx % N4;
+        float v = 0.0f;
+        if (n < NOUT) {
+            const float r = S[((size_t)b * T + t) * NOUT + n] - Y[((size_t)b * T + t) * NOUT + n] * s_inv[n];
+            v = gscale * r;
+            l = r * r;
+        } else if (n < NOUT + NH && have_dh) {
+            const float h = __bfloat162float(Hrow[(size_t)b * K0 + NIN + (n - NOUT)]);
+            v = dZ[(size_t)b * K0 + NIN + (n - NOUT)] * (1.0f - h * h);
+        }
+        dO[idx] = __float2bfloat16(v);
+    }
+    // loss partial sums
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) l += __shfl_xor_sync(0xffffffffu, l, d);
+    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss_acc, (double)l);
+}
+
+// column sums of a [rows x N] bf16 matrix into g (FP32, accumulate)
+__global__ void k_colsum(const __nv_bfloat16 *__restrict__ X, long rows, int N, float *g) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const long r0 = (long)blockIdx.y * 2048, r1 = min(rows, r0 + 2048);
+    float s = 0.0f;
+    for (long r = r0; r < r1; r++) s += __bfloat162float(X[r * N + n]);
+    atomicAdd(&g[n], s);
+}
+
+// AdamW on the master weights, then the BF16 copies W (K x N) and W^T (N x K)
+__global__ void k_adamw(float *theta, const float *__restrict__ grad, float *m, float *v, int n, float lr, float wd,
+                        float b1, float b2, float bc1, float bc2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / bc1, vh = vi / bc2;
+    theta[i] -= lr * (mh / (sqrtf(vh) + eps) + wd * theta[i]);
+}
+
+__global__ void k_cast_weights(const float *__restrict__ theta, __nv_bfloat16 *W, __nv_bfloat16 *Wt, int off, int K,
+                               int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * N) return;
+    const int k = i / N, nn = i % N;
+    const __nv_bfloat16 b = __float2bfloat16(theta[off + i]);
+    W[i] = b;
+    Wt[(size_t)nn * K + k] = b;
+}
+
+// ensemble statistics of one increment: mean over members and relative spread
+__global__ void k_ensemble(const float *__restrict__ Sm, int n_members, int n, float s_floor, float *mean,
+                           float *spread) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float mu[NOUT], var = 0.0f, nrm = 0.0f;
+    for (int c = 0; c < NOUT; c++) {
+        float s = 0.0f;
+        for (int k = 0; k < n_members; k++) s += Sm[((size_t)k * n + i) * NOUT + c];
+        mu[c] = s / n_members;
+        float q = 0.0f;
+        for (int k = 0; k < n_members; k++) {
+            const float d = Sm[((size_t)k * n + i) * NOUT + c] - mu[c];
+            q += d * d;
+        }
+        var += n_members > 1 ? q / (n_members - 1) : 0.0f;
+        nrm += mu[c] * mu[c];
+        mean[(size_t)i * NOUT + c] = mu[c];
+    }
+    spread[i] = sqrtf(var) / fmaxf(sqrtf(nrm), s_floor);
+}
+
+__global__ void k_h_to_input(const float *__restrict__ h, int n, __nv_bfloat16 *Z) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * NH) return;
+    const int b = idx / NH, k = idx % NH;
+    Z[(size_t)b * K0 + NIN + k] = __float2bfloat16(h[idx]);
+}
+
+inline int cdiv(long a, int b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct SurMember {
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *W[4] = {nullptr}, *Wt[4] = {nullptr};
+    int step = 0;
+};
+
+struct sur_ctx {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int K = 0, Bmax = 0, Tmax = 0;
+    std::vector<SurMember> mem;
+    std::vector<void *> allocs;
+    float *u_inv = nullptr, *s_inv = nullptr, *s_mul = nullptr;
+    float h_u_scale[NIN], h_s_scale[NOUT];
+    // activations (T x B rows)
+    __nv_bfloat16 *Z = nullptr, *Y1 = nullptr, *A1 = nullptr, *Y2 = nullptr, *A2 = nullptr, *Y3 = nullptr,
+                  *A3 = nullptr, *dO = nullptr, *dY3 = nullptr, *dY2 = nullptr, *dY1 = nullptr;
+    float *S = nullptr, *dZ = nullptr, *Sm = nullptr;
+    double *loss_acc = nullptr;
+};
+
+namespace {
+const int KDIM[4] = {K0, WID, WID, WID}, NDIM[4] = {WID, WID, WID, N4};
+const int WOFF[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4}, BOFF[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
+
+template <class T>
+cudaError_t salloc(sur_ctx *s, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    s->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return cudaMemsetAsync(q, 0, std::max<size_t>(n, 1) * sizeof(T), s->stream);
+}
+
+void cast_member(sur_ctx *s, SurMember &M) {
+    for (int l = 0; l < 4; l++)
+        k_cast_weights<<<cdiv((long)KDIM[l] * NDIM[l], 256), 256, 0, s->stream>>>(M.theta, M.W[l], M.Wt[l], WOFF[l],
+                                                                                  KDIM[l], NDIM[l]);
+}
+
+// forward through T steps for member M; stress predictions into S (B x T x 6)
+void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, const float *s_mul) {
+    const size_t RB = (size_t)B;
+    for (int t = 0; t < T; t++) {
+        __nv_bfloat16 *Zt = s->Z + (size_t)t * RB * K0;
+        k_build_input<<<cdiv(RB * K0, 256), 256, 0, s->stream>>>(U, B, T, t, s->u_inv, Zt, t == 0);
+        Epi e{};
+        e.ld_out = WID;
+        const __nv_bfloat16 *in = Zt;
+        int kin = K0;
+        __nv_bfloat16 *Ys[3] = {s->Y1, s->Y2, s->Y3}, *As_[3] = {s->A1, s->A2, s->A3};
+        for (int l = 0; l < 3; l++) {
+            e.bias = M.theta + BOFF[l];
+            e.y_out = Ys[l] + (size_t)t * RB * WID;
+            e.a_out = As_[l] + (size_t)t * RB * WID;
+            gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, B, WID, kin, e);
+            in = e.a_out;
+            kin = WID;
+        }
+        Epi h{};
+        h.bias = M.theta + OFF_B4;
+        h.s_out = S + (size_t)t * NOUT;
+        h.s_ld = T * NOUT;
+        h.s_mul = s_mul;  // null during training: the loss works in network units
+        h.h_next = (t + 1 < T) ? s->Z + (size_t)(t + 1) * RB * K0 : nullptr;
+        h.h_f32 = nullptr;
+        gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, B, N4, WID, h);
+    }
+}
+
+// BPTT: gradient into M.grad (zeroed here); returns nothing (loss into loss_acc)
+void backward(sur_ctx *s, SurMember &M, const float *Y, int B, int T, const float *S) {
+    const size_t RB = (size_t)B;
+    cudaMemsetAsync(M.grad, 0, sizeof(float) * NPAR, s->stream);
+    const float gscale = 2.0f / ((float)B * T * NOUT);
+    for (int t = T - 1; t >= 0; t--) {
+        __nv_bfloat16 *dOt = s->dO + (size_t)t * RB * N4;
+        const __nv_bfloat16 *Hrow = (t + 1 < T) ? s->Z + (size_t)(t + 1) * RB * K0 : s->Z;
+        k_head_grad<<<cdiv(RB * N4, 256), 256, 0, s->stream>>>(S, Y, B, T, t, s->s_inv, Hrow, s->dZ, t + 1 < T,
+                                                              gscale, dOt, s->loss_acc);
+        Epi e{};
+        e.ld_out = WID;
+        e.ld_in = WID;
+        // dY3 = (dO W4^T) * gelu'(Y3)
+        e.y_in = s->Y3 + (size_t)t * RB * WID;
+        e.a_out = s->dY3 + (size_t)t * RB * WID;
+        gemm<EPI_DGELU, false>(s->stream, dOt, N4, M.Wt[3], WID, B, WID, N4, e);
+        e.y_in = s->Y2 + (size_t)t * RB * WID;
+        e.a_out = s->dY2 + (size_t)t * RB * WID;
+        gemm<EPI_DGELU, false>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.Wt[2], WID, B, WID, WID, e);
+        e.y_in = s->Y1 + (size_t)t * RB * WID;
+        e.a_out = s->dY1 + (size_t)t * RB * WID;
+        gemm<EPI_DGELU, false>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.Wt[1], WID, B, WID, WID, e);
+        if (t > 0) {  // dZ = dY1 W1^T (only the state part is used by step t-1)
+            Epi f{};
+            f.s_out = s->dZ;
+            f.s_ld = K0;
+            gemm<EPI_F32, false>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.Wt[0], K0, B, K0, WID, f);
+        }
+    }
+    // weight gradients over all steps at once: dW = op(A_all)^T dY_all (split-K)
+    const long rows = (long)T * B;
+    const int split = (int)std::min<long>(16, std::max<long>(1, rows / 4096));
+    const __nv_bfloat16 *Ain[4] = {s->Z, s->A1, s->A2, s->A3};
+    const __nv_bfloat16 *dOut[4] = {s->dY1, s->dY2, s->dY3, s->dO};
+    for (int l = 0; l < 4; l++) {
+        Epi w{};
+        w.s_out = M.grad + WOFF[l];
+        w.s_ld = NDIM[l];
+        gemm<EPI_WGRAD, true>(s->stream, Ain[l], KDIM[l], dOut[l], NDIM[l], KDIM[l], NDIM[l], (int)rows, w, split);
+        dim3 g(cdiv(NDIM[l], 128), cdiv(rows, 2048));
+        k_colsum<<<g, 128, 0, s->stream>>>(dOut[l], rows, NDIM[l], M.grad + BOFF[l]);
+    }
+}
+
+int init_member(sur_ctx *s, SurMember &M, uint64_t seed) {
+    // seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from a splitmix64
+    // stream, zero biases and zero padding rows / columns
+    std::vector<float> th(NPAR, 0.0f);
+    uint64_t x = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    auto next = [&]() {
+        x += 0x9E3779B97F4A7C15ull;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < 4; l++) {
+        const double lim = 1.0 / std::sqrt((double)KDIM[l]);
+        for (int k = 0; k < KDIM[l]; k++)
+            for (int n = 0; n < NDIM[l]; n++) {
+                float w = (float)((2.0 * next() - 1.0) * lim);
+                if (l == 0 && k >= NIN + NH) w = 0.0f;
+                if (l == 3 && n >= NOUT + NH) w = 0.0f;
+                th[WOFF[l] + (size_t)k * NDIM[l] + n] = w;
+            }
+    }
+    if (cudaMemcpyAsync(M.theta, th.data(), sizeof(float) * NPAR, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return RC_ECUDA;
+    cudaMemsetAsync(M.m, 0, sizeof(float) * NPAR, s->stream);
+    cudaMemsetAsync(M.v, 0, sizeof(float) * NPAR, s->stream);
+    M.step = 0;
+    cast_member(s, M);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void *stream, sur_ctx **out) {
+    if (!out || n_members <= 0 || max_batch <= 0 || max_steps <= 0) return RC_EINVAL;
+    *out = nullptr;
+    sur_ctx *s = new sur_ctx();
+    s->K = n_members;
+    s->Bmax = max_batch;
+    s->Tmax = max_steps;
+    if (stream) s->stream = (cudaStream_t)stream;
+    else if (cudaStreamCreate(&s->stream) != cudaSuccess) { delete s; return RC_ECUDA; }
+    else s->own_stream = true;
+    const size_t R = (size_t)max_batch * max_steps;
+    bool ok = true;
+    ok &= salloc(s, &s->u_inv, NIN) == cudaSuccess;
+    ok &= salloc(s, &s->s_inv, NOUT) == cudaSuccess;
+    ok &= salloc(s, &s->s_mul, NOUT) == cudaSuccess;
+    ok &= salloc(s, &s->Z, R * K0 + (size_t)max_batch * K0) == cudaSuccess;
+    for (__nv_bfloat16 **p : {&s->Y1, &s->A1, &s->Y2, &s->A2, &s->Y3, &s->A3, &s->dY3, &s->dY2, &s->dY1})
+        ok &= salloc(s, p, R * WID) == cudaSuccess;
+    ok &= salloc(s, &s->dO, R * N4) == cudaSuccess;
+    ok &= salloc(s, &s->S, R * NOUT * (size_t)n_members) == cudaSuccess;
+    ok &= salloc(s, &s->Sm, (size_t)max_batch * NOUT * n_members) == cudaSuccess;
+    ok &= salloc(s, &s->dZ, (size_t)max_batch * K0) == cudaSuccess;
+    ok &= salloc(s, &s->loss_acc, 1) == cudaSuccess;
+    s->mem.resize(n_members);
+    for (auto &M : s->mem) {
+        ok &= salloc(s, &M.theta, NPAR) == cudaSuccess;
+        ok &= salloc(s, &M.grad, NPAR) == cudaSuccess;
+        ok &= salloc(s, &M.m, NPAR) == cudaSuccess;
+        ok &= salloc(s, &M.v, NPAR) == cudaSuccess;
+        for (int l = 0; l < 4; l++) {
+            ok &= salloc(s, &M.W[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
+            ok &= salloc(s, &M.Wt[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
+        }
+    }
+    if (!ok) { sur_destroy(s); return RC_ENOMEM; }
+    float one[NIN];
+    for (int k = 0; k < NIN; k++) one[k] = 1.0f;
+    if (sur_set_scaling(s, one, one) != RC_OK) { sur_destroy(s); return RC_ECUDA; }
+    for (int k = 0; k < n_members; k++)
+        if (init_member(s, s->mem[k], seed + (uint64_t)k) != RC_OK) { sur_destroy(s); return RC_ECUDA; }
+    *out = s;
+    return RC_OK;
+}
+
+int sur_set_scaling(sur_ctx *s, const float *u_scale, const float *s_scale) {
+    if (!s || !u_scale || !s_scale) return RC_EINVAL;
+    float ui[NIN], si[NOUT], sm[NOUT];
+    for (int k = 0; k < NIN; k++) {
+        if (!(u_scale[k] > 0)) return RC_EINVAL;
+        ui[k] = 1.0f / u_scale[k];
+        s->h_u_scale[k] = u_scale[k];
+    }
+    for (int k = 0; k < NOUT; k++) {
+        if (!(s_scale[k] > 0)) return RC_EINVAL;
+        si[k] = 1.0f / s_scale[k];
+        sm[k] = s_scale[k];
+        s->h_s_scale[k] = s_scale[k];
+    }
+    cudaMemcpyAsync(s->u_inv, ui, sizeof ui, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->s_inv, si, sizeof si, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->s_mul, sm, sizeof sm, cudaMemcpyHostToDevice, s->stream);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_get_params(sur_ctx *s, int member, float *theta) {
+    if (!s || !theta || member < 0 || member >= s->K) return RC_EINVAL;
+    if (cudaMemcpyAsync(theta, s->mem[member].theta, sizeof(float) * NPAR, cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return RC_ECUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_set_params(sur_ctx *s, int member, const float *theta) {
+    if (!s || !theta || member < 0 || member >= s->K) return RC_EINVAL;
+    SurMember &M = s->mem[member];
+    if (cudaMemcpyAsync(M.theta, theta, sizeof(float) * NPAR, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        return RC_ECUDA;
+    cudaMemsetAsync(M.m, 0, sizeof(float) * NPAR, s->stream);
+    cudaMemsetAsync(M.v, 0, sizeof(float) * NPAR, s->stream);
+    M.step = 0;
+    cast_member(s, M);
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+static int check_batch(sur_ctx *s, int B, int T) {
+    if (B <= 0 || T <= 0 || B > s->Bmax || T > s->Tmax) return RC_EINVAL;
+    return RC_OK;
+}
+
+int sur_loss_grad(sur_ctx *s, int member, const float *U, const float *Y, int B, int T, double *loss, float *grad) {
+    if (!s || !U || !Y || member < 0 || member >= s->K) return RC_EINVAL;
+    if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
+    SurMember &M = s->mem[member];
+    cudaMemsetAsync(s->loss_acc, 0, sizeof(double), s->stream);
+    forward(s, M, U, B, T, s->S, nullptr);
+    backward(s, M, Y, B, T, s->S);
+    double l = 0.0;
+    cudaMemcpyAsync(&l, s->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (grad) cudaMemcpyAsync(grad, M.grad, sizeof(float) * NPAR, cudaMemcpyDeviceToHost, s->stream);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return RC_ECUDA;
+    if (loss) *loss = l / ((double)B * T * NOUT);
+    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_train_step(sur_ctx *s, const float *U, const float *Y, int B, int T, float lr, float wd, double *loss) {
+    if (!s || !U || !Y) return RC_EINVAL;
+    if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
+    std::vector<double> l(s->K, 0.0);
+    for (int k = 0; k < s->K; k++) {
+        SurMember &M = s->mem[k];
+        cudaMemsetAsync(s->loss_acc, 0, sizeof(double), s->stream);
+        forward(s, M, U, B, T, s->S, nullptr);
+        backward(s, M, Y, B, T, s->S);
+        M.step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float bc1 = 1.0f - std::pow(b1, (float)M.step), bc2 = 1.0f - std::pow(b2, (float)M.step);
+        k_adamw<<<cdiv(NPAR, 256), 256, 0, s->stream>>>(M.theta, M.grad, M.m, M.v, NPAR, lr, wd, b1, b2, bc1, bc2,
+                                                        1e-8f);
+        cast_member(s, M);
+        if (loss) cudaMemcpyAsync(&l[k], s->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    }
+    if (loss) {
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return RC_ECUDA;
+        for (int k = 0; k < s->K; k++) loss[k] = l[k] / ((double)B * T * NOUT);
+    }
+    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_predict(sur_ctx *s, const float *U, int B, int T, float *Sout) {
+    if (!s || !U || !Sout) return RC_EINVAL;
+    if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
+    for (int k = 0; k < s->K; k++) forward(s, s->mem[k], U, B, T, Sout + (size_t)k * B * T * NOUT, s->s_mul);
+    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *s_mean, float *spread) {
+    if (!s || !u || !h || !s_mean || !spread || n <= 0 || n > s->Bmax) return RC_EINVAL;
+    __nv_bfloat16 *Z = s->Z;  // n rows of [u, h, 0]
+    __nv_bfloat16 *Ys[3] = {s->Y1, s->Y2, s->Y3}, *As_[3] = {s->A1, s->A2, s->A3};
+    for (int k = 0; k < s->K; k++) {
+        SurMember &M = s->mem[k];
+        float *hk = h + (size_t)k * n * NH;
+        k_build_input<<<cdiv((long)n * K0, 256), 256, 0, s->stream>>>(u, n, 1, 0, s->u_inv, Z, 0);
+        k_h_to_input<<<cdiv((long)n * NH, 256), 256, 0, s->stream>>>(hk, n, Z);
+        const __nv_bfloat16 *in = Z;
+        int kin = K0;
+        for (int l = 0; l < 3; l++) {
+            Epi e{};
+            e.ld_out = WID;
+            e.bias = M.theta + BOFF[l];
+            e.y_out = Ys[l];
+            e.a_out = As_[l];
+            gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, n, WID, kin, e);
+            in = As_[l];
+            kin = WID;
+        }
+        Epi hd{};
+        hd.bias = M.theta + OFF_B4;
+        hd.s_out = s->Sm + (size_t)k * n * NOUT;
+        hd.s_ld = NOUT;
+        hd.s_mul = s->s_mul;
+        hd.h_next = nullptr;
+        hd.h_f32 = hk;  // the new state replaces the old one (the input row holds a BF16 copy)
+        gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, n, N4, WID, hd);
+    }
+    k_ensemble<<<cdiv(n, 128), 128, 0, s->stream>>>(s->Sm, s->K, n, s_floor, s_mean, spread);
+    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+void sur_destroy(sur_ctx *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

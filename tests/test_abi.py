@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    txt = open(os.path.join(ROOT, "include", "rcell.h")).read()
+    txt = "".join(open(os.path.join(ROOT, "include", f)).read()
+                  for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = re.findall(r"^\s*(?:int|void|const\s+char\s*\*)\s*\**\s*(\w+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
@@ -35,10 +36,12 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_binding_mirrors_the_header():
-    from paper_1902_09171_gb300 import rcell
-    assert sorted(rcell.EXPORTS) == header_functions()
+    from paper_1902_09171_gb300 import rcell, surrogate
+    assert sorted(rcell.EXPORTS + surrogate.EXPORTS) == header_functions()
     for name in rcell.EXPORTS:
         assert callable(getattr(rcell, name)), name
+    for name in surrogate.EXPORTS:
+        assert callable(getattr(surrogate, name)), name
 
 
 def test_product_path_never_touches_the_oracle():
