@@ -79,7 +79,9 @@ enum { RC_UNITS_METAL = 0, RC_UNITS_LJ = 1 };
  * thermostat with damping time tau (tau <= 0: none), temperature kT (energy
  * units), noise from Philox4x32-10 keyed by `seed`.  skin: Verlet-list skin
  * (r_list = rc + skin); lists are rebuilt when an atom has moved more than
- * skin/2 since the last build. */
+ * skin/2 since the last build.  max_step > 0 limits every atom's displacement
+ * per step to max_step by rescaling its half-step velocity (a soft start for
+ * overlapping initial states; 0 = off). */
 typedef struct {
     int potential;       /* RC_POT_*                                           */
     int units;           /* RC_UNITS_*                                         */
@@ -89,6 +91,7 @@ typedef struct {
     double skin;
     double mass, kT, tau, dt;
     uint64_t seed;
+    double max_step;
 } rcell_params;
 
 /* One r-cell's initial state (host memory).
@@ -127,6 +130,12 @@ int rcell_set_deformation(rcell_ctx *ctx, const double *F, int where);
  * the last n_avg steps (0 <= n_avg <= n_steps).  Captured into a CUDA graph
  * per (n_steps, n_avg) after its first use.  Asynchronous. */
 int rcell_run(rcell_ctx *ctx, int n_steps, int n_avg);
+
+/* Per-cell activity mask (n_cells ints, `where` memory): cells with mask 0 are
+ * skipped by rcell_set_deformation, rcell_run and rcell_eval -- their atoms, box,
+ * R(t-1) and random-stream counter stay as they are -- until re-enabled.  All
+ * cells start active.  Asynchronous for device masks. */
+int rcell_set_active(rcell_ctx *ctx, const int *mask, int where);
 
 /* Time-averaged stress of the last rcell_run, per cell:
  *   sigma        n_cells x 6: mean of Q sigma_MD(t) Q^T over the sampled steps
@@ -261,6 +270,29 @@ int fe_update(fe_ctx *fe, const double *P, int where);
  * r-cell batch must hold one cell per element.  u_out: nn x 3 host doubles or
  * NULL (synchronous when given).  Everything else stays on the device. */
 int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, double *u_out);
+
+/* One FE step with the learned surrogate and MD fallback (the paper's Fig. 1
+ * loop with the r-cell MD replaced where the ensemble agrees).  For every
+ * element: surrogate input from (F_prev, F) and one recurrent step of every
+ * member (include/surrogate.h); points whose ensemble spread exceeds spread_on
+ * -- or exceeded it before and still exceed spread_off -- or all points when
+ * force_md != 0, run n_steps of r-cell MD (rcell_set_active masks the rest) and
+ * use its P; the others use P = J sigma_sur F^{-T}.  Then the FE update.
+ *   h_state  device, n_members x ne x 128 floats: recurrent states (zero to start)
+ *   F_prev   device, ne x 9 doubles: F of the previous step (identity to start);
+ *            overwritten with this step's F
+ *   md_flag  device, ne ints: 1 where MD was used (read for the hysteresis, then
+ *            overwritten)
+ *   n_md     host, may be NULL: number of points that ran MD
+ * fe, rc and sur must share one CUDA stream.  Synchronises once per step (to
+ * skip the MD launches when no point needs them). */
+int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, struct sur_ctx *sur, double lambda, int n_steps, int n_avg,
+                      float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
+                      int *md_flag, int *n_md);
+
+/* First Piola-Kirchhoff stresses (ne x 9) used by the last FE update, into
+ * `where` memory.  Synchronous when where == RC_HOST. */
+int fe_get_P(fe_ctx *fe, double *P, int where);
 
 /* Displacements and velocities (nn x 3 each, host; either may be NULL). */
 int fe_get_state(fe_ctx *fe, double *d, double *v);

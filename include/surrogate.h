@@ -76,6 +76,15 @@ int sur_predict(sur_ctx *s, const float *U, int B, int T, float *S);
  * Asynchronous. */
 int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *s_mean, float *spread);
 
+/* Surrogate input of one increment for n points: u = (F - F_prev row-major (9),
+ * Green strain E = (F^T F - I)/2 in Voigt order xx yy zz xy xz yz (6)).
+ * F_prev, F: device n x 9 doubles; u: device n x 15 floats.  Asynchronous on
+ * `stream`. */
+int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream);
+
+/* Number of members and the stream of a surrogate context (either may be NULL). */
+int sur_info(const sur_ctx *s, int *n_members, void **stream);
+
 void sur_destroy(sur_ctx *s);
 
 #ifdef __cplusplus

@@ -137,3 +137,13 @@ def adamw(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01
     vh = v / (1.0 - beta2 ** step)
     theta = theta - lr * (mh / (np.sqrt(vh) + eps) + wd * theta)
     return theta, m, v
+
+
+def features(F_prev, F):
+    """Surrogate input of one increment: (F - F_prev) row-major (9) and the Green
+    strain E = (F^T F - I)/2 in Voigt order xx yy zz xy xz yz (6)."""
+    F_prev = np.asarray(F_prev, dtype=np.float64).reshape(-1, 3, 3)
+    F = np.asarray(F, dtype=np.float64).reshape(-1, 3, 3)
+    E = 0.5 * (np.einsum("nki,nkj->nij", F, F) - np.eye(3))
+    v = np.stack([E[:, 0, 0], E[:, 1, 1], E[:, 2, 2], E[:, 0, 1], E[:, 0, 2], E[:, 1, 2]], axis=1)
+    return np.concatenate([(F - F_prev).reshape(-1, 9), v], axis=1)

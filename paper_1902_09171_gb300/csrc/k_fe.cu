@@ -126,7 +126,68 @@ __global__ void k_update(const int *__restrict__ mask, const double *__restrict_
     d[q] += dt * vn;
 }
 
+// MD-fallback decision per quadrature point (hysteresis): MD when the ensemble
+// spread exceeds `on`, or when the point was on MD and the spread still exceeds `off`
+__global__ void k_decide(const float *__restrict__ spread, float on, float off, int force_md, int *md_flag, int *n_md,
+                         int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const float sp = spread[e];
+    const int md = force_md || !(sp <= on) || (md_flag[e] && !(sp <= off));
+    md_flag[e] = md;
+    if (md) atomicAdd(n_md, 1);
+}
+
+// P = J sigma F^{-T} from the surrogate stress (FE frame) where the point is not on MD
+__global__ void k_merge_P(const int *__restrict__ md_flag, const float *__restrict__ s_sur, const double *__restrict__ F,
+                          const double *__restrict__ P_md, double *P, int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    if (md_flag[e]) {
+        for (int k = 0; k < 9; k++) P[9 * e + k] = P_md[9 * e + k];
+        return;
+    }
+    const double *Fe = F + 9 * e;
+    const double J = Fe[0] * (Fe[4] * Fe[8] - Fe[5] * Fe[7]) - Fe[1] * (Fe[3] * Fe[8] - Fe[5] * Fe[6]) +
+                     Fe[2] * (Fe[3] * Fe[7] - Fe[4] * Fe[6]);
+    double Fi[9];
+    Fi[0] = (Fe[4] * Fe[8] - Fe[5] * Fe[7]) / J;
+    Fi[1] = (Fe[2] * Fe[7] - Fe[1] * Fe[8]) / J;
+    Fi[2] = (Fe[1] * Fe[5] - Fe[2] * Fe[4]) / J;
+    Fi[3] = (Fe[5] * Fe[6] - Fe[3] * Fe[8]) / J;
+    Fi[4] = (Fe[0] * Fe[8] - Fe[2] * Fe[6]) / J;
+    Fi[5] = (Fe[2] * Fe[3] - Fe[0] * Fe[5]) / J;
+    Fi[6] = (Fe[3] * Fe[7] - Fe[4] * Fe[6]) / J;
+    Fi[7] = (Fe[1] * Fe[6] - Fe[0] * Fe[7]) / J;
+    Fi[8] = (Fe[0] * Fe[4] - Fe[1] * Fe[3]) / J;
+    const float *sv = s_sur + 6 * e;
+    const double S[9] = {sv[0], sv[3], sv[4], sv[3], sv[1], sv[5], sv[4], sv[5], sv[2]};
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; l++) acc += S[3 * i + l] * Fi[3 * j + l];
+            P[9 * e + 3 * i + j] = J * acc;
+        }
+}
+
+__global__ void k_copy_F(const double *__restrict__ F, double *F_prev, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) F_prev[i] = F[i];
+}
+
 }  // namespace
+
+void fe_launch_surrogate_merge(const int *md_flag, const float *s_sur, const double *F, const double *P_md, double *P,
+                               int ne, cudaStream_t s) {
+    k_merge_P<<<(ne + 127) / 128, 128, 0, s>>>(md_flag, s_sur, F, P_md, P, ne);
+}
+void fe_launch_decide(const float *spread, float on, float off, int force_md, int *md_flag, int *n_md, int ne,
+                      cudaStream_t s) {
+    k_decide<<<(ne + 127) / 128, 128, 0, s>>>(spread, on, off, force_md, md_flag, n_md, ne);
+}
+void fe_launch_copy_F(const double *F, double *F_prev, int ne, cudaStream_t s) {
+    k_copy_F<<<(9 * ne + 255) / 256, 256, 0, s>>>(F, F_prev, 9 * ne);
+}
 
 void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
                         double *mass, int *err, cudaStream_t s) {

@@ -62,7 +62,7 @@ template <int TPA, bool M6>
 __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, int cur) {
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
-    if (a.status[c] != 0) return;
+    if (a.status[c] != 0 || !a.active[c]) return;
     __shared__ ShiftTab s_tab;
     __shared__ float s_H[8];
     rc_load_shifts(s_tab, s_H, a.Hf, c);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
                                                        int step_index) {
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
-    if (a.status[c] != 0) return;
+    if (a.status[c] != 0 || !a.active[c]) return;
     __shared__ ShiftTab s_tab;
     __shared__ float s_H[8];
     rc_load_shifts(s_tab, s_H, a.Hf, c);
@@ -302,6 +302,15 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
             vv.x = fmaf(hdt, ax, vv.x);
             vv.y = fmaf(hdt, ay, vv.y);
             vv.z = fmaf(hdt, az, vv.z);
+            if (p.max_step > 0.0f) {
+                const float s2 = p.dt * p.dt * (vv.x * vv.x + vv.y * vv.y + vv.z * vv.z);
+                if (s2 > p.max_step * p.max_step) {
+                    const float f = p.max_step * rsqrtf(s2);
+                    vv.x *= f;
+                    vv.y *= f;
+                    vv.z *= f;
+                }
+            }
             float4 xn = make_float4(fmaf(p.dt, vv.x, xi.x), fmaf(p.dt, vv.y, xi.y), fmaf(p.dt, vv.z, xi.z), 0.0f);
             a.v[g] = vv;
             (cur ? a.x0 : a.x1)[g] = xn;

@@ -14,12 +14,13 @@ __device__ __forceinline__ double det3(const double *A) {
 // one thread per cell
 __global__ void k_deform(const double *__restrict__ Fin, double *H, double *Rprev, double *Qo, double *Ro,
                          double *Fst, double *dR, const double *__restrict__ H0, float *Hf, float *Hif, int *status,
-                         int *need_rebuild, int *nbins, const int *bin_cap, double rlist, int n_cells) {
+                         int *need_rebuild, int *nbins, const int *bin_cap, const int *active, double rlist,
+                         int n_cells) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     double *dRc = dR + 9 * c;
     for (int k = 0; k < 9; k++) dRc[k] = (k % 4 == 0) ? 1.0 : 0.0;  // identity unless the cell is updated
-    if (status[c] != 0) return;
+    if (status[c] != 0 || !active[c]) return;  // inactive cells keep box, R(t-1) and atoms
     double F[9];
     for (int k = 0; k < 9; k++) F[k] = Fin[9 * c + k];
     if (!(det3(F) > 0.0)) {
@@ -116,7 +117,7 @@ __global__ void k_deform(const double *__restrict__ Fin, double *H, double *Rpre
 __global__ void k_remap(KArrays a, const double *__restrict__ dR, int cur) {
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
-    if (a.status[c] != 0) return;
+    if (a.status[c] != 0 || !a.active[c]) return;
     const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
     if (li >= a.cell_n[c]) return;
     const int g = a.cell_off[c] + li;
@@ -243,18 +244,18 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(const double *__restr
     }
 }
 
-__global__ void k_advance(unsigned long long *evals, int n_cells, int n) {
+__global__ void k_advance(unsigned long long *evals, const int *active, int n_cells, int n) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_cells) evals[c] += (unsigned long long)n;
+    if (c < n_cells && active[c]) evals[c] += (unsigned long long)n;
 }
 
 }  // namespace
 
 void rc_launch_deform_impl(const double *F, double *H, double *Rprev, double *Q, double *R, double *Fst, double *dR,
                            const double *H0, float *Hf, float *Hif, int *status, int *need_rebuild, int *nbins,
-                           const int *bin_cap, double rlist, int n_cells, cudaStream_t s) {
+                           const int *bin_cap, const int *active, double rlist, int n_cells, cudaStream_t s) {
     k_deform<<<(n_cells + 127) / 128, 128, 0, s>>>(F, H, Rprev, Q, R, Fst, dR, H0, Hf, Hif, status, need_rebuild,
-                                                   nbins, bin_cap, rlist, n_cells);
+                                                   nbins, bin_cap, active, rlist, n_cells);
 }
 
 void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, cudaStream_t s) {
@@ -268,6 +269,6 @@ void rc_launch_stress(const double *series, int n_avg, int series_cap, const dou
                                                 sig_se, sig_md, P);
 }
 
-void rc_launch_advance(unsigned long long *evals, int n_cells, int n, cudaStream_t s) {
-    k_advance<<<(n_cells + 127) / 128, 128, 0, s>>>(evals, n_cells, n);
+void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s) {
+    k_advance<<<(n_cells + 127) / 128, 128, 0, s>>>(evals, active, n_cells, n);
 }

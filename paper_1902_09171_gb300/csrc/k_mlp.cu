@@ -281,6 +281,25 @@ __global__ void k_h_to_input(const float *__restrict__ h, int n, __nv_bfloat16 *
     Z[(size_t)b * K0 + NIN + k] = __float2bfloat16(h[idx]);
 }
 
+// surrogate input of one increment: u = (F - F_prev (row-major, 9), E = (F^T F - I)/2 in
+// Voigt order xx yy zz xy xz yz (6))
+__global__ void k_features(const double *__restrict__ Fp, const double *__restrict__ F, int n, float *u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *f = F + 9 * i, *fp = Fp + 9 * i;
+    float *o = u + (size_t)i * NIN;
+    for (int k = 0; k < 9; k++) o[k] = (float)(f[k] - fp[k]);
+    double C[9];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) C[3 * a + b] = f[a] * f[b] + f[3 + a] * f[3 + b] + f[6 + a] * f[6 + b];
+    o[9] = (float)(0.5 * (C[0] - 1.0));
+    o[10] = (float)(0.5 * (C[4] - 1.0));
+    o[11] = (float)(0.5 * (C[8] - 1.0));
+    o[12] = (float)(0.5 * C[1]);
+    o[13] = (float)(0.5 * C[2]);
+    o[14] = (float)(0.5 * C[5]);
+}
+
 inline int cdiv(long a, int b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
@@ -607,6 +626,19 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
     }
     k_ensemble<<<cdiv(n, 128), 128, 0, s->stream>>>(s->Sm, s->K, n, s_floor, s_mean, spread);
     return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream) {
+    if (!F_prev || !F || !u || n <= 0) return RC_EINVAL;
+    k_features<<<cdiv(n, 128), 128, 0, (cudaStream_t)stream>>>(F_prev, F, n, u);
+    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_info(const sur_ctx *s, int *n_members, void **stream) {
+    if (!s) return RC_EINVAL;
+    if (n_members) *n_members = s->K;
+    if (stream) *stream = (void *)s->stream;
+    return RC_OK;
 }
 
 void sur_destroy(sur_ctx *s) {

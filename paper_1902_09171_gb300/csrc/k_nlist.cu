@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     __shared__ int s_cnt[RC_MAX_BINS_PER_CELL];
     __shared__ int s_go;
     if (threadIdx.x == 0) {
-        int go = a.need_rebuild[c] && a.status[c] == 0;
+        int go = a.need_rebuild[c] && a.status[c] == 0 && a.active[c];
         a.built[c] = go;
         if (go) a.need_rebuild[c] = 0;
         s_go = go;

@@ -45,6 +45,7 @@ struct KParams {
     float mvv2e;          // m v^2 -> energy units, times mass (per atom)
     uint64_t seed;
     int max_nb;
+    float max_step;       // > 0: displacement limit per step
 };
 
 struct KArrays {
@@ -57,6 +58,7 @@ struct KArrays {
     int *bin_start;      // bin_off[c] .. + nbins+1
     int *status;
     int *need_rebuild, *built;
+    const int *active;   // per cell: 0 = skipped by every MD kernel (state frozen)
     const unsigned long long *evals;
     double *series;      // [cell][slot][RC_SAMPLE_W]
     int series_cap;
@@ -155,12 +157,12 @@ void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, i
                      int step_index, cudaStream_t s);
 void rc_launch_deform_impl(const double *F, double *H, double *Rprev, double *Q, double *R, double *Fst, double *dR,
                            const double *H0, float *Hf, float *Hif, int *status, int *need_rebuild, int *nbins,
-                           const int *bin_cap, double rlist, int n_cells, cudaStream_t s);
+                           const int *bin_cap, const int *active, double rlist, int n_cells, cudaStream_t s);
 void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, cudaStream_t s);
 void rc_launch_stress(const double *series, int n_avg, int series_cap, const double *H, const double *Q,
                       const double *F, double pconv, double *rot_scratch, double *sig_fem, double *sig_se,
                       double *sig_md, double *P, int n_cells, cudaStream_t s);
-void rc_launch_advance(unsigned long long *evals, int n_cells, int n, cudaStream_t s);
+void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s);
 
 // finite elements (k_fe.cu)
 void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
@@ -172,3 +174,8 @@ void fe_launch_fint(const double *X, const int *conn, const double *gradN, const
                     const double *d, double hg, double *fint, int ne, cudaStream_t s);
 void fe_launch_update(const int *mask, const double *mass, const double *fint, double dt, double damping,
                       double *d, double *v, int n3, cudaStream_t s);
+void fe_launch_surrogate_merge(const int *md_flag, const float *s_sur, const double *F, const double *P_md, double *P,
+                               int ne, cudaStream_t s);
+void fe_launch_decide(const float *spread, float on, float off, int force_md, int *md_flag, int *n_md, int ne,
+                      cudaStream_t s);
+void fe_launch_copy_F(const double *F, double *F_prev, int ne, cudaStream_t s);

@@ -11,6 +11,7 @@
 #include <tuple>
 #include <vector>
 
+#include "../../include/surrogate.h"
 #include "rc_internal.cuh"
 
 namespace {
@@ -63,6 +64,10 @@ struct fe_ctx {
     double *d_d = nullptr, *d_v = nullptr, *d_fint = nullptr, *d_F = nullptr, *d_P = nullptr;
     int *d_conn = nullptr, *d_mask = nullptr, *d_err = nullptr;
     cudaEvent_t ev = nullptr;
+    // surrogate-coupled steps (allocated on first use)
+    float *d_u = nullptr, *d_smean = nullptr, *d_spread = nullptr;
+    double *d_Pmd = nullptr;
+    int *d_nmd = nullptr;
     std::string err = "ok";
 };
 
@@ -134,7 +139,7 @@ long enqueue_run(rcell_ctx *c, int n_steps, int n_avg) {
         k += enqueue_step(c, mode, slot, s);
         if (mode != MODE_LAST) c->cur ^= 1;
     }
-    rc_launch_advance(c->d_evals, c->n_cells, n_steps + 1, c->stream);
+    rc_launch_advance(c->d_evals, c->ka.active, c->n_cells, n_steps + 1, c->stream);
     return k + 1;
 }
 
@@ -249,6 +254,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     kp.mvv2e = (float)(P.mass / ftm2v);
     kp.seed = P.seed;
     kp.max_nb = max_nb;
+    kp.max_step = P.max_step > 0 ? (float)P.max_step : 0.0f;
 
     // ---- device memory ----
     KArrays &A = c->ka;
@@ -266,6 +272,13 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     CKC(c, dalloc(L, &A.status, n_cells));
     CKC(c, dalloc(L, &A.need_rebuild, n_cells));
     CKC(c, dalloc(L, &A.built, n_cells));
+    int *d_active = nullptr;
+    CKC(c, dalloc(L, &d_active, n_cells));
+    {
+        std::vector<int> ones(n_cells, 1);
+        CKC(c, cudaMemcpy(d_active, ones.data(), sizeof(int) * n_cells, cudaMemcpyHostToDevice));
+    }
+    A.active = d_active;
     CKC(c, dalloc(L, &c->d_evals, n_cells));
     CKC(c, dalloc(L, &A.eval_acc, 8 * (size_t)n_cells));
     CKC(c, dalloc(L, &c->d_H, 9 * (size_t)n_cells));
@@ -357,7 +370,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     CKC(c, cudaMemcpy(c->d_Fin, hI.data(), sizeof(double) * 9 * n_cells, cudaMemcpyHostToDevice));
     // initial box: the deformation kernel with F = I sets H = H0, the FP32 box copies and the bins
     rc_launch_deform_impl(c->d_Fin, c->d_H, c->d_Rprev, c->d_Q, c->d_R, c->d_F, c->d_dR, c->d_H0, c->d_Hf, c->d_Hif,
-                          A.status, A.need_rebuild, c->d_nbins, c->d_bin_cap, c->rlist, n_cells, c->stream);
+                          A.status, A.need_rebuild, c->d_nbins, c->d_bin_cap, A.active, c->rlist, n_cells, c->stream);
     CKC(c, cudaGetLastError());
     int st = first_status(c);
     if (st != RC_OK) {
@@ -379,7 +392,7 @@ int rcell_set_deformation(rcell_ctx *c, const double *F, int where) {
         return fail(c, RC_EINVAL, "where");
     }
     rc_launch_deform_impl(dF, c->d_H, c->d_Rprev, c->d_Q, c->d_R, c->d_F, c->d_dR, c->d_H0, c->d_Hf, c->d_Hif,
-                          c->ka.status, c->ka.need_rebuild, c->d_nbins, c->d_bin_cap, c->rlist, c->n_cells, c->stream);
+                          c->ka.status, c->ka.need_rebuild, c->d_nbins, c->d_bin_cap, c->ka.active, c->rlist, c->n_cells, c->stream);
     rc_launch_remap(c->ka, c->d_dR, c->cur, c->n_tiles, c->stream);
     CKC(c, cudaGetLastError());
     return RC_OK;
@@ -417,6 +430,14 @@ int rcell_run(rcell_ctx *c, int n_steps, int n_avg) {
         CKC(c, cudaGetLastError());
     }
     c->last_n_avg = n_avg;
+    return RC_OK;
+}
+
+int rcell_set_active(rcell_ctx *c, const int *mask, int where) {
+    if (!c || !mask) return RC_EINVAL;
+    CKC(c, cudaMemcpyAsync((void *)c->ka.active, mask, sizeof(int) * c->n_cells,
+                           where == RC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    if (where == RC_HOST) CKC(c, cudaStreamSynchronize(c->stream));
     return RC_OK;
 }
 
@@ -659,7 +680,7 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
     // coupling kernels once: re-apply the current F (Delta R = I), then the stress reduction
     CKC(c, cudaEventRecord(ev[0], c->stream));
     rc_launch_deform_impl(c->d_F, c->d_H, c->d_Rprev, c->d_Q, c->d_R, c->d_F, c->d_dR, c->d_H0, c->d_Hf, c->d_Hif,
-                          c->ka.status, c->ka.need_rebuild, c->d_nbins, c->d_bin_cap, c->rlist, c->n_cells, c->stream);
+                          c->ka.status, c->ka.need_rebuild, c->d_nbins, c->d_bin_cap, c->ka.active, c->rlist, c->n_cells, c->stream);
     CKC(c, cudaEventRecord(ev[1], c->stream));
     rc_launch_remap(c->ka, c->d_dR, c->cur, c->n_tiles, c->stream);
     CKC(c, cudaEventRecord(ev[2], c->stream));
@@ -684,7 +705,7 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
         if (s > 0) lap(3, 4, 3);  // steady-state force launches only
         if (mode != MODE_LAST) c->cur ^= 1;
     }
-    rc_launch_advance(c->d_evals, c->n_cells, n_steps + 1, c->stream);
+    rc_launch_advance(c->d_evals, c->ka.active, c->n_cells, n_steps + 1, c->stream);
     if (c->last_n_avg > 0) {
         CKC(c, cudaEventRecord(ev[0], c->stream));
         rc_launch_stress(c->ka.series, c->last_n_avg, c->series_cap, c->d_H, c->d_Q, c->d_F, pconv_of(c->prm.units),
@@ -820,6 +841,65 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
         CKF(fe, cudaStreamSynchronize(fe->stream));
         return rcell_sync(rc);
     }
+    return RC_OK;
+}
+
+int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, int n_steps, int n_avg,
+                      float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
+                      int *md_flag, int *n_md) {
+    if (!fe || !rc || !sur || !h_state || !F_prev || !md_flag) return RC_EINVAL;
+    if (rc->n_cells != fe->ne) { fe->err = "one r-cell per element required"; return RC_EINVAL; }
+    void *ss = nullptr;
+    if (sur_info(sur, nullptr, &ss) != RC_OK) return RC_EINVAL;
+    if ((cudaStream_t)ss != fe->stream || rc->stream != fe->stream) {
+        fe->err = "fe, r-cell and surrogate contexts must share one stream";
+        return RC_EINVAL;
+    }
+    const int ne = fe->ne;
+    cudaStream_t st = fe->stream;
+    if (!fe->d_u) {
+        CKF(fe, dalloc(fe->allocs, &fe->d_u, 15 * (size_t)ne));
+        CKF(fe, dalloc(fe->allocs, &fe->d_smean, 6 * (size_t)ne));
+        CKF(fe, dalloc(fe->allocs, &fe->d_spread, ne));
+        CKF(fe, dalloc(fe->allocs, &fe->d_Pmd, 9 * (size_t)ne));
+        CKF(fe, dalloc(fe->allocs, &fe->d_nmd, 1));
+    }
+    int e;
+    // 1. boundary conditions and element F
+    fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, st);
+    fe_launch_F(fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, ne, st);
+    // 2. surrogate for every point (keeps every recurrent state current)
+    if ((e = sur_features(F_prev, fe->d_F, ne, fe->d_u, st)) != RC_OK) return e;
+    if ((e = sur_step(sur, fe->d_u, ne, h_state, s_floor, fe->d_smean, fe->d_spread)) != RC_OK) return e;
+    // 3. which points fall back to MD
+    CKF(fe, cudaMemsetAsync(fe->d_nmd, 0, sizeof(int), st));
+    fe_launch_decide(fe->d_spread, spread_on, spread_off, force_md, md_flag, fe->d_nmd, ne, st);
+    int nmd = 0;
+    CKF(fe, cudaMemcpyAsync(&nmd, fe->d_nmd, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKF(fe, cudaStreamSynchronize(st));
+    // 4. MD for the flagged points only (the others keep their frozen r-cell state;
+    //    a point that returns to MD takes the whole deformation since its last MD
+    //    increment in one remap)
+    if (nmd > 0) {
+        if ((e = rcell_set_active(rc, md_flag, RC_DEVICE)) != RC_OK) return e;
+        if ((e = rcell_set_deformation(rc, fe->d_F, RC_DEVICE)) != RC_OK) return e;
+        if ((e = rcell_run(rc, n_steps, n_avg)) != RC_OK) return e;
+        if ((e = rcell_stress(rc, nullptr, nullptr, fe->d_Pmd, RC_DEVICE)) != RC_OK) return e;
+    }
+    // 5. merge: MD P where flagged, J sigma_sur F^-T elsewhere; then the FE update
+    fe_launch_surrogate_merge(md_flag, fe->d_smean, fe->d_F, fe->d_Pmd, fe->d_P, ne, st);
+    fe_launch_copy_F(fe->d_F, F_prev, ne, st);
+    CKF(fe, cudaGetLastError());
+    if ((e = fe_update(fe, fe->d_P, RC_DEVICE)) != RC_OK) return e;
+    if (n_md) *n_md = nmd;
+    return RC_OK;
+}
+
+int fe_get_P(fe_ctx *fe, double *P, int where) {
+    if (!fe || !P) return RC_EINVAL;
+    CKF(fe, cudaMemcpyAsync(P, fe->d_P, sizeof(double) * 9 * fe->ne,
+                            where == RC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, fe->stream));
+    if (where == RC_HOST) CKF(fe, cudaStreamSynchronize(fe->stream));
     return RC_OK;
 }
 

@@ -196,3 +196,43 @@ def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
         if worst < 0.12:
             break
     return np.mod(x, L)
+
+
+def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, max_shear: float = 0.08):
+    """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I):
+    a mix of monotone and cyclic uniaxial stretch along x (amplitude up to
+    max_strain in tension, half of it in compression), lateral strain
+    -nu * eps_x with nu drawn in [0, 0.5], plus a monotone simple shear
+    F_xy up to max_shear.  Returns an (n_paths, n_inc + 1, 3, 3) array."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(n_inc + 1) / n_inc
+    F = np.tile(np.eye(3), (n_paths, n_inc + 1, 1, 1))
+    for p in range(n_paths):
+        amp = rng.uniform(-0.5 * max_strain, max_strain)
+        if rng.uniform() < 0.5:
+            ex = amp * t
+        else:
+            cycles = rng.integers(1, 4)
+            ex = amp * np.sin(np.pi * cycles * t) * t ** 0.5
+        nu = rng.uniform(0.0, 0.5)
+        gam = rng.uniform(-max_shear, max_shear) * t
+        F[p, :, 0, 0] = 1.0 + ex
+        F[p, :, 1, 1] = 1.0 - nu * ex
+        F[p, :, 2, 2] = 1.0 - nu * ex
+        F[p, :, 0, 1] = gam
+    return F
+
+
+def kg_cells(n_cells: int, n_chains: int, chain_len: int, density: float, seed: int, n_distinct: int = 4):
+    """n_cells Kremer-Grest r-cells built from n_distinct seeded melts, each copy
+    shifted by a seeded random periodic translation (positions wrapped).  Returns
+    a list of dicts (H0, x0, bonds)."""
+    rng = np.random.default_rng(seed)
+    melts = [kg_melt(n_chains, chain_len, density, seed=seed * 1000 + k) for k in range(n_distinct)]
+    cells = []
+    for c in range(n_cells):
+        x, H, b = melts[c % n_distinct]
+        L = H[0, 0]
+        xs = np.mod(x + rng.uniform(0, L, 3), L)
+        cells.append(dict(H0=H.copy(), x0=to_f32(xs), bonds=b))
+    return cells

@@ -35,7 +35,8 @@ class rcell_params(C.Structure):
     _fields_ = [("potential", C.c_int), ("units", C.c_int), ("eps", C.c_double), ("sigma", C.c_double),
                 ("rc", C.c_double), ("n", C.c_double), ("m", C.c_double), ("c", C.c_double),
                 ("k_fene", C.c_double), ("R0", C.c_double), ("skin", C.c_double), ("mass", C.c_double),
-                ("kT", C.c_double), ("tau", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64)]
+                ("kT", C.c_double), ("tau", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
+                ("max_step", C.c_double)]
 
 
 class rcell_init(C.Structure):
@@ -46,8 +47,8 @@ class rcell_init(C.Structure):
 _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
-           "rcell_clear_status", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
-           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step",
+           "rcell_clear_status", "rcell_set_active", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
+           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
 
@@ -74,6 +75,7 @@ def load(path: str | None = None):
         "rcell_get_series": ([vp, C.c_int, vp, vp, vp], C.c_int),
         "rcell_sync": ([vp], C.c_int),
         "rcell_clear_status": ([vp], C.c_int),
+        "rcell_set_active": ([vp, vp, C.c_int], C.c_int),
         "rcell_set_tuning": ([vp, C.c_int, C.c_int], C.c_int),
         "rcell_info": ([vp, I, C.POINTER(C.c_long), C.POINTER(C.c_long)], C.c_int),
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
@@ -88,6 +90,9 @@ def load(path: str | None = None):
         "fe_get_F": ([vp, vp, C.c_int], C.c_int),
         "fe_update": ([vp, vp, C.c_int], C.c_int),
         "fe_step": ([vp, vp, C.c_double, C.c_int, C.c_int, vp], C.c_int),
+        "fe_step_surrogate": ([vp, vp, vp, C.c_double, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, C.c_int,
+                               vp, vp, vp, C.POINTER(C.c_int)], C.c_int),
+        "fe_get_P": ([vp, vp, C.c_int], C.c_int),
         "fe_get_state": ([vp, vp, vp], C.c_int),
         "fe_destroy": ([vp], None),
     }
@@ -236,6 +241,16 @@ def rcell_clear_status(ctx):
     _check(load().rcell_clear_status(ctx), ctx, "rcell_clear_status")
 
 
+def rcell_set_active(ctx, mask):
+    """mask: host int array or CUDA int32 tensor, one entry per cell (0 = frozen)."""
+    if hasattr(mask, "data_ptr"):
+        p, where, keep = _arr_ptr(mask)
+    else:
+        keep = np.ascontiguousarray(mask, dtype=np.int32)
+        p, where = C.c_void_p(keep.ctypes.data), RC_HOST
+    _check(load().rcell_set_active(ctx, p, where), ctx, "rcell_set_active")
+
+
 def rcell_set_tuning(ctx, threads_per_atom: int = -1, use_graphs: int = -1):
     _check(load().rcell_set_tuning(ctx, threads_per_atom, use_graphs), ctx, "rcell_set_tuning")
 
@@ -319,6 +334,22 @@ def fe_step(fe, rc, lam: float, n_steps: int, n_avg: int, u_out=None):
     _check(load().fe_step(fe, rc, lam, n_steps, n_avg, p), rc, "fe_step")
 
 
+def fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, force_md, h_state, F_prev,
+                      md_flag):
+    """Device state tensors: h_state (float32, members x ne x 128), F_prev (float64,
+    ne x 3 x 3), md_flag (int32, ne).  Returns the number of points that ran MD."""
+    n = C.c_int(0)
+    ptr = [C.c_void_p(t.data_ptr()) for t in (h_state, F_prev, md_flag)]
+    _check(load().fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, int(force_md),
+                                    ptr[0], ptr[1], ptr[2], C.byref(n)), rc, "fe_step_surrogate")
+    return n.value
+
+
+def fe_get_P(fe, P):
+    p, where, keep = _arr_ptr(P)
+    _check(load().fe_get_P(fe, p, where), None, "fe_get_P")
+
+
 def fe_get_state(fe, nn: int):
     d, v = np.zeros((nn, 3)), np.zeros((nn, 3))
     _check(load().fe_get_state(fe, C.c_void_p(d.ctypes.data), C.c_void_p(v.ctypes.data)), None, "fe_get_state")
@@ -348,6 +379,7 @@ def params_sc_cu(tau=0.1, kT=None, dt=0.002, seed=1, skin=1.5):
                         kT, tau, dt, seed)
 
 
-def params_kg(tau=2.0, kT=0.3, dt=0.005, seed=1, skin=0.3):
+def params_kg(tau=2.0, kT=0.3, dt=0.005, seed=1, skin=0.3, max_step=0.0):
     """Kremer-Grest bead-spring (reduced units): LJ rc = 2.5, FENE k = 30, R0 = 1.5; gamma = 1/tau."""
-    return rcell_params(RC_POT_KG, RC_UNITS_LJ, 1.0, 1.0, 2.5, 0, 0, 0, 30.0, 1.5, skin, 1.0, kT, tau, dt, seed)
+    return rcell_params(RC_POT_KG, RC_UNITS_LJ, 1.0, 1.0, 2.5, 0, 0, 0, 30.0, 1.5, skin, 1.0, kT, tau, dt, seed,
+                        max_step)

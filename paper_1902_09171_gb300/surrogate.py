@@ -14,7 +14,7 @@ from . import rcell
 SUR_N_IN, SUR_N_H, SUR_N_OUT, SUR_WIDTH = 15, 128, 6, 256
 SUR_N_PARAMS = 144 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 144 + 144
 EXPORTS = ["sur_create", "sur_set_scaling", "sur_get_params", "sur_set_params", "sur_loss_grad", "sur_train_step",
-           "sur_predict", "sur_step", "sur_destroy"]
+           "sur_predict", "sur_step", "sur_features", "sur_info", "sur_destroy"]
 _bound = False
 
 
@@ -32,6 +32,8 @@ def _lib():
             "sur_train_step": ([vp, vp, vp, C.c_int, C.c_int, C.c_float, C.c_float, vp], C.c_int),
             "sur_predict": ([vp, vp, C.c_int, C.c_int, vp], C.c_int),
             "sur_step": ([vp, vp, C.c_int, vp, C.c_float, vp, vp], C.c_int),
+            "sur_features": ([vp, vp, C.c_int, vp, vp], C.c_int),
+            "sur_info": ([vp, C.POINTER(C.c_int), C.POINTER(vp)], C.c_int),
             "sur_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
@@ -103,6 +105,18 @@ def sur_predict(s, U, out):
 
 def sur_step(s, u, h, s_floor, s_mean, spread):
     _chk(_lib().sur_step(s, _dp(u), int(u.shape[0]), _dp(h), s_floor, _dp(s_mean), _dp(spread)), "sur_step")
+
+
+def sur_features(F_prev, F, u, stream=None):
+    """F_prev, F: CUDA float64 (n, 3, 3); u: CUDA float32 (n, 15) output."""
+    _chk(_lib().sur_features(_dp(F_prev), _dp(F), int(F.shape[0]), _dp(u), rcell._stream_ptr(stream)), "sur_features")
+
+
+def sur_info(s):
+    k = C.c_int(0)
+    st = C.c_void_p()
+    _chk(_lib().sur_info(s, C.byref(k), C.byref(st)), "sur_info")
+    return k.value, st.value
 
 
 def sur_destroy(s):

@@ -105,3 +105,21 @@ def test_descent_on_a_fitting_problem():
         theta, m, v = mlp.adamw(theta, g, m, v, s, 3e-3)
     assert mlp.loss(theta, U, Y) < 0.2 * L0
     assert math.isfinite(L)
+
+
+def test_features_closed_forms():
+    # pure rotation: no strain; identical F: no increment; uniaxial stretch: E_xx = (l^2 - 1)/2
+    th = 0.4
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    u = mlp.features(R, R)
+    assert np.abs(u).max() < 1e-15
+    lam = 1.2
+    u = mlp.features(np.eye(3), np.diag([lam, 1.0, 1.0]))
+    assert abs(u[0, 9] - 0.5 * (lam * lam - 1)) < 1e-15 and np.abs(u[0, 10:]).max() == 0.0
+    assert abs(u[0, 0] - (lam - 1)) < 1e-15
+    # simple shear F = I + g e_x e_y: E_xy = g/2, E_yy = g^2/2
+    g = 0.1
+    F = np.eye(3)
+    F[0, 1] = g
+    u = mlp.features(np.eye(3), F)
+    assert abs(u[0, 12] - g / 2) < 1e-15 and abs(u[0, 10] - g * g / 2) < 1e-15
