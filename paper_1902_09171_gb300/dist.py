@@ -1,0 +1,56 @@
+"""Multi-GPU layout of the r-cell batch (one process per GPU).
+
+The r-cells of a load step are independent at the MD level (Sec. 2.2: the
+paper gives each r-cell its own communicator split), so the cells are split
+into contiguous, atom-balanced shards, one per rank, with no collective on the
+MD data path.  The only exchange is the FE-level one of Sec. 2.2 (scatter F,
+gather the stress): each rank contributes the stresses of its own cells and
+`gather_cells` assembles the full per-cell array on every rank.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def shard_by_atoms(n_atoms_per_cell, world: int):
+    """Contiguous split of the cells into `world` shards with nearly equal atom
+    counts (greedy prefix cut).  Returns a list of (first, last+1) per rank."""
+    n = np.asarray(n_atoms_per_cell, dtype=np.int64)
+    total = int(n.sum())
+    cuts = [0]
+    acc = 0
+    r = 1
+    for i, a in enumerate(n):
+        acc += int(a)
+        while r < world and acc >= r * total / world and len(cuts) == r:
+            cuts.append(i + 1)
+            r += 1
+    while len(cuts) < world:
+        cuts.append(len(n))
+    cuts.append(len(n))
+    return [(cuts[k], cuts[k + 1]) for k in range(world)]
+
+
+def gather_cells(local, bounds, group=None):
+    """All-gather per-cell rows (torch tensor, local cells x k) into the full array
+    ordered by cell, on every rank."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    counts = [b - a for a, b in bounds]
+    width = local.shape[1:]
+    pad = max(counts)
+    buf = torch.zeros((pad,) + tuple(width), dtype=local.dtype, device=local.device)
+    buf[:local.shape[0]] = local
+    parts = [torch.zeros_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    return torch.cat([p[:c] for p, c in zip(parts, counts)], dim=0)
+
+
+def max_over_ranks(value: float, group=None) -> float:
+    """Largest value over all ranks (the timing rule: the slowest rank sets the time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
