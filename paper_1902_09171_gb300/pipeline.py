@@ -54,7 +54,11 @@ def prepare_kg_batch(n_cells, n_chains=100, chain_len=50, density=0.85, seed=3, 
     st = rcell.rcell_sync(ctx)
     if st != 0:
         raise rcell.RCellError(st, "equilibration: " + rcell.rcell_last_error(ctx))
-    return ctx, eq_cells
+    final = []
+    for k, c in enumerate(eq_cells):
+        x, v, _ = rcell.rcell_get_atoms(ctx, k, len(c["x0"]))
+        final.append(dict(H0=c["H0"], x0=x, v0=v, bonds=c["bonds"]))
+    return ctx, final
 
 
 def generate_dataset(ctx, F_paths, n_steps, n_avg, stream=None):
@@ -105,14 +109,21 @@ def train(sur, U, Y, steps, lr=1e-3, wd=0.01, n_members=4, log_every=0):
     return losses
 
 
-def relative_error(sur, U, Y, n_members):
-    """RMS error of the ensemble-mean prediction over the RMS of the targets."""
+def relative_error(sur, U, Y, n_members, s_floor=0.0, with_spread=False):
+    """RMS error of the ensemble-mean prediction over the RMS of the targets; with
+    with_spread, also quantiles of the ensemble spread
+    ||std over members|| / max(||mean||, s_floor) over all (path, increment)."""
     torch = _torch()
     B, T = U.shape[0], U.shape[1]
     out = torch.zeros((n_members, B, T, 6), dtype=torch.float32, device=U.device)
     S.sur_predict(sur, U, out)
     mean = out.mean(0)
-    return float(((mean - Y) ** 2).mean().sqrt() / (Y ** 2).mean().sqrt())
+    err = float(((mean - Y) ** 2).mean().sqrt() / (Y ** 2).mean().sqrt())
+    if not with_spread:
+        return err
+    sd = out.std(0, unbiased=True).norm(dim=-1) / mean.norm(dim=-1).clamp_min(s_floor)
+    q = torch.quantile(sd.flatten().float(), torch.tensor([0.1, 0.5, 0.9, 0.99], device=sd.device))
+    return err, [float(v) for v in q]
 
 
 def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n_avg, spread_on=0.02,
