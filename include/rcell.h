@@ -281,14 +281,16 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
  *   h_state  device, n_members x ne x 128 floats: recurrent states (zero to start)
  *   F_prev   device, ne x 9 doubles: F of the previous step (identity to start);
  *            overwritten with this step's F
- *   md_flag  device, ne ints: 1 where MD was used (read for the hysteresis, then
- *            overwritten)
+ *   md_flag  device, ne ints: 0 surrogate, 1 MD because the spread tripped, 2 MD
+ *            because force_md was set (read for the hysteresis, which only
+ *            keeps tripped points on MD; then overwritten)
+ *   spread_out device, ne floats or NULL: the ensemble spread of every point
  *   n_md     host, may be NULL: number of points that ran MD
  * fe, rc and sur must share one CUDA stream.  Synchronises once per step (to
  * skip the MD launches when no point needs them). */
 int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, struct sur_ctx *sur, double lambda, int n_steps, int n_avg,
                       float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
-                      int *md_flag, int *n_md);
+                      int *md_flag, float *spread_out, int *n_md);
 
 /* First Piola-Kirchhoff stresses (ne x 9) used by the last FE update, into
  * `where` memory.  Synchronous when where == RC_HOST. */

@@ -126,16 +126,19 @@ __global__ void k_update(const int *__restrict__ mask, const double *__restrict_
     d[q] += dt * vn;
 }
 
-// MD-fallback decision per quadrature point (hysteresis): MD when the ensemble
-// spread exceeds `on`, or when the point was on MD and the spread still exceeds `off`
+// MD-fallback decision per quadrature point with hysteresis: a point trips to MD
+// when the ensemble spread exceeds `on` and, once tripped, stays on MD while the
+// spread exceeds `off`.  Flags: 0 surrogate, 1 tripped (MD), 2 forced MD
+// (start-up increments; a forced point is not tripped).
 __global__ void k_decide(const float *__restrict__ spread, float on, float off, int force_md, int *md_flag, int *n_md,
                          int ne) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const float sp = spread[e];
-    const int md = force_md || !(sp <= on) || (md_flag[e] && !(sp <= off));
-    md_flag[e] = md;
-    if (md) atomicAdd(n_md, 1);
+    const int tripped = !(sp <= on) || (md_flag[e] == 1 && !(sp <= off));
+    const int flag = tripped ? 1 : (force_md ? 2 : 0);
+    md_flag[e] = flag;
+    if (flag) atomicAdd(n_md, 1);
 }
 
 // P = J sigma F^{-T} from the surrogate stress (FE frame) where the point is not on MD

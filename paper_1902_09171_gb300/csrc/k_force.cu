@@ -28,31 +28,46 @@ __device__ __forceinline__ float sub_sum(float v) {
     return v;
 }
 
-// Walk one atom's Verlet list (this lane's share: entries sub, sub+TPA, ...),
-// U entries at a time: the U list words are loaded first, then the U neighbour
-// positions, then the U pair evaluations run -- U independent memory requests in
-// flight per thread instead of one.  fn(xj, d) receives the neighbour's record
-// and the exact periodic displacement d = x_j(image) - x_i.
-constexpr int RC_UNROLL = 4;
+// Walk one atom's Verlet list (this lane's share: groups sub, sub+TPA, ... of
+// four entries).  Each group is one 16-byte load; the next group is requested
+// before the current one is processed, and the four neighbour positions of a
+// group are gathered before any pair is evaluated, so several memory requests
+// are in flight per thread.  fn(xj, d) receives the neighbour's record and the
+// exact periodic displacement d = x_j(image) - x_i.
 template <int TPA, class Fn>
-__device__ __forceinline__ void for_each_neighbor(const int *__restrict__ nb, int nn, int sub,
+__device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub,
                                                   const float4 *__restrict__ XG, const float4 &xi, const ShiftTab &T,
                                                   Fn &&fn) {
-    int k = sub;
-    for (; k + (RC_UNROLL - 1) * TPA < nn; k += RC_UNROLL * TPA) {
-        unsigned e[RC_UNROLL];
-        float4 xj[RC_UNROLL];
+    const int ng = (nn + 3) >> 2;
+    int g = sub;
+    if (g >= ng) return;
+    int4 e = __ldg(nb4 + (size_t)g * RC_TILE);
+    while (true) {
+        const int gn = g + TPA;
+        int4 en = e;
+        if (gn < ng) en = __ldg(nb4 + (size_t)gn * RC_TILE);
+        const int left = nn - 4 * g;
+        if (left >= 4) {
+            const float4 x0 = __ldg(XG + ((unsigned)e.x & RC_IDX_MASK));
+            const float4 x1 = __ldg(XG + ((unsigned)e.y & RC_IDX_MASK));
+            const float4 x2 = __ldg(XG + ((unsigned)e.z & RC_IDX_MASK));
+            const float4 x3 = __ldg(XG + ((unsigned)e.w & RC_IDX_MASK));
+            fn(x0, rc_disp(xi, x0, T, (unsigned)e.x >> RC_IDX_BITS));
+            fn(x1, rc_disp(xi, x1, T, (unsigned)e.y >> RC_IDX_BITS));
+            fn(x2, rc_disp(xi, x2, T, (unsigned)e.z >> RC_IDX_BITS));
+            fn(x3, rc_disp(xi, x3, T, (unsigned)e.w >> RC_IDX_BITS));
+        } else {
+            const unsigned ee[3] = {(unsigned)e.x, (unsigned)e.y, (unsigned)e.z};
 #pragma unroll
-        for (int u = 0; u < RC_UNROLL; u++) e[u] = (unsigned)__ldg(nb + (size_t)(k + u * TPA) * RC_TILE);
-#pragma unroll
-        for (int u = 0; u < RC_UNROLL; u++) xj[u] = __ldg(XG + (e[u] & RC_IDX_MASK));
-#pragma unroll
-        for (int u = 0; u < RC_UNROLL; u++) fn(xj[u], rc_disp(xi, xj[u], T, e[u] >> RC_IDX_BITS));
-    }
-    for (; k < nn; k += TPA) {
-        const unsigned e = (unsigned)__ldg(nb + (size_t)k * RC_TILE);
-        const float4 xj = __ldg(XG + (e & RC_IDX_MASK));
-        fn(xj, rc_disp(xi, xj, T, e >> RC_IDX_BITS));
+            for (int u = 0; u < 3; u++)
+                if (u < left) {
+                    const float4 xj = __ldg(XG + (ee[u] & RC_IDX_MASK));
+                    fn(xj, rc_disp(xi, xj, T, ee[u] >> RC_IDX_BITS));
+                }
+        }
+        if (gn >= ng) break;
+        e = en;
+        g = gn;
     }
 }
 
@@ -78,7 +93,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     if (live) {
         xi = X[g];
         const int nn = a.nnb[g];
-        const int *__restrict__ nb = a.nbr + (size_t)t * p.max_nb * RC_TILE + at;
+        const int4 *__restrict__ nb = reinterpret_cast<const int4 *>(a.nbr) + (size_t)t * (p.max_nb / 4) * RC_TILE + at;
         const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m;
         const float rc2 = p.rc2;
         for_each_neighbor<TPA>(nb, nn, sub, X, xi, s_tab, [&](const float4 &, const float3 &d) {
@@ -140,7 +155,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
     if (live) {
         xi = XG[g];
         const int nn = a.nnb[g];
-        const int *__restrict__ nb = a.nbr + (size_t)t * p.max_nb * RC_TILE + at;
+        const int4 *__restrict__ nb = reinterpret_cast<const int4 *>(a.nbr) + (size_t)t * (p.max_nb / 4) * RC_TILE + at;
         if (POT == RC_POT_SC) {
             const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m, hn = 0.5f * p.sc_n;
             const float cm2 = 0.5f * p.sc_c * p.sc_m;

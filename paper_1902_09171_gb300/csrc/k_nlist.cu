@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
     const float4 *X = cur ? a.x1 : a.x0;
-    int *nbr = a.nbr + (size_t)t * p.max_nb * RC_TILE + threadIdx.x;
+    // entry k of this atom lives at word 4 * ((t * max_nb/4 + k/4) * TILE + lane) + k%4
+    int *nbr = a.nbr + (size_t)t * p.max_nb * RC_TILE + 4 * threadIdx.x;
     int cnt = 0;
     if (li < n) {
         const int g = off + li;
@@ -203,7 +204,8 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                         const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
                         if (r2 < p.rlist2) {
                             if (cnt < p.max_nb)
-                                nbr[(size_t)cnt * RC_TILE] = (int)((unsigned)(off + jl) | ((unsigned)code << RC_IDX_BITS));
+                                nbr[(size_t)(cnt >> 2) * (4 * RC_TILE) + (cnt & 3)] =
+                                    (int)((unsigned)(off + jl) | ((unsigned)code << RC_IDX_BITS));
                             cnt++;
                         }
                     }

@@ -10,9 +10,10 @@
 //     writes x(t+dt) of its own atoms).  Velocities: float4 {vx, vy, vz, 0}.
 //   * Inside a cell, atoms are kept sorted by neighbour bin (counting sort at
 //     every list rebuild); `tag` maps a slot back to the caller's atom index.
-//   * Verlet list: per tile, column-major [TILE][max_nb] int32 entries
-//     j_global | (image << 27); the image code 0..26 selects one of the 27
-//     periodic shift vectors of the cell.
+//   * Verlet list: per tile, [max_nb/4][TILE] groups of four int32 entries
+//     j_global | (image << 27) (one 16-byte load per lane per group, coalesced
+//     across the tile); the image code 0..26 selects one of the 27 periodic
+//     shift vectors of the cell.
 //   * Per-cell FP64 state: box H, stretch R(t-1), Q, R, F of the last
 //     deformation, Philox force-evaluation counter, status word.
 #pragma once

@@ -527,7 +527,7 @@ int rcell_get_neighbors(rcell_ctx *c, int cell, int *pairs, long max_pairs, long
     for (int i = 0; i < n; i++) {
         const int t = i / RC_TILE, l = i % RC_TILE;
         for (int q = 0; q < nnb[i]; q++) {
-            const unsigned e = (unsigned)nbr[((size_t)t * mx + q) * RC_TILE + l];
+            const unsigned e = (unsigned)nbr[((size_t)t * mx + (q & ~3)) * RC_TILE + 4 * l + (q & 3)];
             const int j = (int)(e & RC_IDX_MASK) - off;
             if (j < 0 || j >= n) return fail(c, RC_ESTATE, "neighbour index outside its cell");
             if (pairs && k < max_pairs) {
@@ -846,7 +846,7 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
 
 int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, int n_steps, int n_avg,
                       float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
-                      int *md_flag, int *n_md) {
+                      int *md_flag, float *spread_out, int *n_md) {
     if (!fe || !rc || !sur || !h_state || !F_prev || !md_flag) return RC_EINVAL;
     if (rc->n_cells != fe->ne) { fe->err = "one r-cell per element required"; return RC_EINVAL; }
     void *ss = nullptr;
@@ -874,6 +874,8 @@ int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, in
     // 3. which points fall back to MD
     CKF(fe, cudaMemsetAsync(fe->d_nmd, 0, sizeof(int), st));
     fe_launch_decide(fe->d_spread, spread_on, spread_off, force_md, md_flag, fe->d_nmd, ne, st);
+    if (spread_out)
+        CKF(fe, cudaMemcpyAsync(spread_out, fe->d_spread, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
     int nmd = 0;
     CKF(fe, cudaMemcpyAsync(&nmd, fe->d_nmd, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKF(fe, cudaStreamSynchronize(st));

@@ -152,18 +152,21 @@ def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n
     h = torch.zeros((n_members, ne, 128), dtype=torch.float32, device=dev)
     Fp = torch.eye(3, dtype=torch.float64, device=dev).repeat(ne, 1, 1).contiguous()
     flag = torch.zeros(ne, dtype=torch.int32, device=dev)
-    P_sg = []
+    spread = torch.zeros(ne, dtype=torch.float32, device=dev)
+    P_sg, sp = [], []
     e0.record(st)
     for k, lam in enumerate(lambdas):
         n = rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
-                                    k < md_first, h, Fp, flag)
+                                    k < md_first, h, Fp, flag, spread)
         rcell.fe_get_P(fe_sg, P)
         P_sg.append(P[:, 0, 0].mean())
+        sp.append(spread.median())
         res["n_md"].append(n)
     e1.record(st)
     torch.cuda.synchronize()
     res["ms_sg"] = e0.elapsed_time(e1)
     res["axial_sg"] = [float(v) for v in P_sg]
+    res["spread_median"] = [float(v) for v in sp]
     a, b = np.array(res["axial_md"]), np.array(res["axial_sg"])
     res["max_rel_dev"] = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30))
     res["md_fraction"] = float(sum(res["n_md"]) / (ne * len(lambdas)))

@@ -91,7 +91,7 @@ def load(path: str | None = None):
         "fe_update": ([vp, vp, C.c_int], C.c_int),
         "fe_step": ([vp, vp, C.c_double, C.c_int, C.c_int, vp], C.c_int),
         "fe_step_surrogate": ([vp, vp, vp, C.c_double, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, C.c_int,
-                               vp, vp, vp, C.POINTER(C.c_int)], C.c_int),
+                               vp, vp, vp, vp, C.POINTER(C.c_int)], C.c_int),
         "fe_get_P": ([vp, vp, C.c_int], C.c_int),
         "fe_get_state": ([vp, vp, vp], C.c_int),
         "fe_destroy": ([vp], None),
@@ -335,13 +335,14 @@ def fe_step(fe, rc, lam: float, n_steps: int, n_avg: int, u_out=None):
 
 
 def fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, force_md, h_state, F_prev,
-                      md_flag):
+                      md_flag, spread_out=None):
     """Device state tensors: h_state (float32, members x ne x 128), F_prev (float64,
-    ne x 3 x 3), md_flag (int32, ne).  Returns the number of points that ran MD."""
+    ne x 3 x 3), md_flag (int32, ne), optional spread_out (float32, ne).
+    Returns the number of points that ran MD."""
     n = C.c_int(0)
-    ptr = [C.c_void_p(t.data_ptr()) for t in (h_state, F_prev, md_flag)]
+    ptr = [None if t is None else C.c_void_p(t.data_ptr()) for t in (h_state, F_prev, md_flag, spread_out)]
     _check(load().fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, int(force_md),
-                                    ptr[0], ptr[1], ptr[2], C.byref(n)), rc, "fe_step_surrogate")
+                                    ptr[0], ptr[1], ptr[2], ptr[3], C.byref(n)), rc, "fe_step_surrogate")
     return n.value
 
 

@@ -86,8 +86,8 @@ def test_fe_step_surrogate_all_md_equals_fe_step(torch):
         nn = a[3].shape[0]
         for k, lam in enumerate([0.002, 0.004]):
             rcell.fe_step(a[1], a[0], lam, 20, 10, None)
-            n = rcell.fe_step_surrogate(b[1], b[0], b[2], lam, 20, 10, 0.02, 0.01, 0.1, 1, h, Fp, flag)
-            assert n == 4
+            n = rcell.fe_step_surrogate(b[1], b[0], b[2], lam, 20, 10, 1e9, 1e9, 0.1, 1, h, Fp, flag)
+            assert n == 4 and int(flag.min()) == 2  # forced, not tripped
         da, _ = rcell.fe_get_state(a[1], nn)
         db, _ = rcell.fe_get_state(b[1], nn)
         assert np.array_equal(da, db)

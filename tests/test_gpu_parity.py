@@ -184,6 +184,17 @@ def test_forces_kremer_grest_melt():
     _eval_and_compare(prm, cells)
 
 
+def test_kremer_grest_uneven_batch():
+    # uneven bead-spring cells (1000, 1500, 2500 beads) in one batch, each with its
+    # own bonds, box and neighbour bins
+    prm = rcell.params_kg()
+    cells = []
+    for k, nch in enumerate((20, 30, 50)):
+        x, H, bonds = inputs.kg_melt(nch, 50, 0.85, seed=40 + k, pushoff_iters=300)
+        cells.append(dict(H0=H, x0=inputs.to_f32(x), bonds=bonds))
+    _eval_and_compare(prm, cells)
+
+
 def test_ragged_batch_of_uneven_cells():
     # cells of 256, 480, 500 and 864 atoms in one batch: tiles of 128 with ragged tails
     prm = rcell.params_lj_cu()
