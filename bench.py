@@ -347,6 +347,118 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_kg_bar(args):
+    """Uneven Kremer-Grest r-cells (sizes U[5000, 20000] beads in chains of 50, seed 3)
+    on a 4x4x4 hex mesh, one FE increment = one bench step (uniaxial tension to 30 %
+    in 60 increments, 1000 MD steps each, last 500 averaged)."""
+    import torch
+
+    from paper_1902_09171_gb300 import build, pipeline, rcell
+    build.build()
+    rcell.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sizes = inputs.uniform_sizes(args.kg_cells, 5000, 20000, 50, 3)
+    cells = []
+    for k, n in enumerate(sizes):
+        x, H, b = inputs.kg_melt(int(n) // 50, 50, 0.85, seed=300 + k, pushoff_iters=args.pushoff)
+        cells.append(dict(H0=H, x0=inputs.to_f32(x), bonds=b))
+    soft = rcell.params_kg(tau=0.5, kT=1.0, dt=0.002, seed=3, max_step=0.02)
+    ctx = rcell.rcell_create(soft, cells, stream=stream)
+    rcell.rcell_run(ctx, 1000, 0)
+    eq = []
+    for k, c in enumerate(cells):
+        x, v, _ = rcell.rcell_get_atoms(ctx, k, len(c["x0"]))
+        eq.append(dict(H0=c["H0"], x0=x, v0=v, bonds=c["bonds"]))
+    rcell.rcell_destroy(ctx)
+    ctx = rcell.rcell_create(rcell.params_kg(), eq, stream=stream)
+    rcell.rcell_set_tuning(ctx, args.tpa or 1, 1)
+    L = float(np.mean([c["H0"][0, 0] for c in cells]))
+    m = int(round(len(cells) ** (1 / 3)))
+    X, conn = inputs.hex_mesh(m, m, m, m * L, m * L, m * L)
+    mask, val = inputs.uniaxial_bc(X, m * L)
+    fe = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=stream)
+    md = args.md_steps
+    for k in range(args.warmup):
+        rcell.fe_step(fe, ctx, 0.3 * (k + 1) / 60, md, md // 2, None)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        rcell.fe_step(fe, ctx, 0.3 * (args.warmup + k + 1) / 60, md, md // 2, None)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    st = rcell.rcell_sync(ctx)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    n_atoms = int(sizes.sum())
+    out = {"metric": "atom-steps/s batched r-cell MD (Kremer-Grest bar, uneven cells)",
+           "value": n_atoms * md * args.steps / (ms / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "status": rcell.STATUS[st], "data": "synthetic",
+           "config": {"workload": f"kg_bar_{len(cells)}_cells_5k_20k", "atoms": n_atoms, "md_steps": md},
+           "fe_load_steps_per_s": args.steps / (ms / 1e3)}
+    rcell.fe_destroy(fe)
+    rcell.rcell_destroy(ctx)
+    return out
+
+
+def run_surrogate_fe(args):
+    """The learned surrogate against plain r-cell MD on an FE bar of Kremer-Grest
+    r-cells (5000 beads each): S1 data generation through batched r-cells, BF16
+    training of a 4-member ensemble, then the same FE load history with all-MD
+    r-cells and with the surrogate + 2 % ensemble-spread MD fallback."""
+    import torch
+
+    from paper_1902_09171_gb300 import build, pipeline, rcell
+    from paper_1902_09171_gb300 import surrogate as S
+    build.build()
+    rcell.load()
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    NP, T, NMD, NAVG, K = args.paths, 60, 400, 300, 4
+    t0 = time.time()
+    ctx, _ = pipeline.prepare_kg_batch(NP, stream=st)
+    F = inputs.strain_paths(NP, T, seed=11)
+    U, Y, data_steps = pipeline.generate_dataset(ctx, F, NMD, NAVG, stream=st)
+    rcell.rcell_destroy(ctx)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    ntr = int(NP * 0.9)
+    sur = S.sur_create(K, NP, T, seed=5, stream=st)
+    us, ys = pipeline.feature_scales(U[:ntr], Y[:ntr])
+    S.sur_set_scaling(sur, us, ys)
+    t0 = time.time()
+    pipeline.train(sur, U[:ntr].contiguous(), Y[:ntr].contiguous(), args.train_steps, lr=1e-3, n_members=K)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    err_ho, spread_q = pipeline.relative_error(sur, U[ntr:].contiguous(), Y[ntr:].contiguous(), K, s_floor=0.2,
+                                               with_spread=True)
+    ne = 32
+    ctx_md, cells = pipeline.prepare_kg_batch(ne, stream=st, seed=21)
+    ctx_sg = rcell.rcell_create(rcell.params_kg(seed=22), cells, stream=st)
+    L = cells[0]["H0"][0, 0]
+    X, conn = inputs.hex_mesh(8, 2, 2, 8 * L, 2 * L, 2 * L)
+    mask, val = inputs.uniaxial_bc(X, 8 * L)
+    fe_md = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=st)
+    fe_sg = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=st)
+    lams = [0.3 * (k + 1) / 60 for k in range(60)]
+    res = pipeline.fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, K, lams, NMD, NAVG, s_floor=0.2, stream=st)
+    for h in (fe_md, fe_sg):
+        rcell.fe_destroy(h)
+    rcell.rcell_destroy(ctx_md)
+    rcell.rcell_destroy(ctx_sg)
+    S.sur_destroy(sur)
+    return {"metric": "FE load-steps/s, surrogate + MD fallback vs all-MD r-cells",
+            "value": len(lams) / (res["ms_sg"] / 1e3), "unit": "load-steps/s", "n_gpus": 1,
+            "all_md_value": len(lams) / (res["ms_md"] / 1e3), "speedup": res["ms_md"] / res["ms_sg"],
+            "max_rel_axial_stress_dev": res["max_rel_dev"], "md_fraction": res["md_fraction"],
+            "heldout_rel_rms_error": err_ho, "heldout_spread_quantiles_10_50_90_99": spread_q,
+            "data_atom_steps": data_steps, "data_s": t_data, "train_s": t_train, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"kg_surrogate_fe_8x2x2_{NP}_paths", "paths": NP, "increments": T,
+                       "md_steps": NMD, "n_avg": NAVG, "members": K, "train_steps": args.train_steps}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,6 +471,11 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe"])
+    ap.add_argument("--kg-cells", type=int, default=64)
+    ap.add_argument("--pushoff", type=int, default=60)
+    ap.add_argument("--paths", type=int, default=1024)
+    ap.add_argument("--train-steps", type=int, default=2500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -366,6 +483,12 @@ def main():
         out = run_reference(args)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.workload != "copper_bar":
+        if args.md_steps == MD_STEPS and args.workload == "kg_bar":
+            args.md_steps = 1000
+        out = run_kg_bar(args) if args.workload == "kg_bar" else run_surrogate_fe(args)
+        print(json.dumps(out))
         return
     out = run_ours(args)
     if out is not None:

@@ -198,12 +198,15 @@ def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
     return np.mod(x, L)
 
 
-def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, max_shear: float = 0.08):
+def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, max_shear: float = 0.08,
+                 jitter: float = 0.01):
     """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I):
     a mix of monotone and cyclic uniaxial stretch along x (amplitude up to
     max_strain in tension, half of it in compression), lateral strain
-    -nu * eps_x with nu drawn in [0, 0.5], plus a monotone simple shear
-    F_xy up to max_shear.  Returns an (n_paths, n_inc + 1, 3, 3) array."""
+    -nu * eps_x with nu drawn in [0, 0.5], a monotone simple shear F_xy up to
+    max_shear, plus a small random ramp (amplitude `jitter`) in all nine
+    components so that every input component is exercised.
+    Returns an (n_paths, n_inc + 1, 3, 3) array."""
     rng = np.random.default_rng(seed)
     t = np.arange(n_inc + 1) / n_inc
     F = np.tile(np.eye(3), (n_paths, n_inc + 1, 1, 1))
@@ -220,6 +223,7 @@ def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, m
         F[p, :, 1, 1] = 1.0 - nu * ex
         F[p, :, 2, 2] = 1.0 - nu * ex
         F[p, :, 0, 1] = gam
+        F[p] += jitter * rng.uniform(-1, 1, (3, 3))[None] * t[:, None, None]
     return F
 
 

@@ -89,10 +89,15 @@ def generate_dataset(ctx, F_paths, n_steps, n_avg, stream=None):
 
 
 def feature_scales(U, Y):
-    """Input scales: per-feature standard deviations (floored).  Output scale: one
-    common RMS over all six stress components, so that components a path barely
-    drives (pure sampling noise) keep their small weight in the loss."""
-    u = U.reshape(-1, U.shape[-1]).std(0).clamp_min(1e-4)
+    """Input scales: per-feature standard deviations, floored at 10 % of the largest
+    one of the same block (the 9 increment components, the 6 strain components), so
+    that a component the training paths barely excite is not blown up to O(1)
+    inputs when a quadrature point does excite it.  Output scale: one common RMS
+    over all six stress components, so that components a path barely drives (pure
+    sampling noise) keep their small weight in the loss."""
+    u = U.reshape(-1, U.shape[-1]).std(0)
+    for a, b in ((0, 9), (9, 15)):
+        u[a:b] = u[a:b].clamp_min(0.1 * float(u[a:b].max()) + 1e-12)
     y = float((Y ** 2).mean().sqrt().clamp_min(1e-4))
     return u.cpu().numpy(), np.full(6, y, dtype=np.float32)
 
