@@ -28,16 +28,75 @@ __device__ __forceinline__ float sub_sum(float v) {
     return v;
 }
 
+// Where neighbour records come from: the global array through the read-only
+// path, or the whole r-cell staged in shared memory (index minus cell offset).
+struct GlobalSrc {
+    const float4 *__restrict__ p;
+    __device__ __forceinline__ float4 operator()(unsigned j) const { return __ldg(p + j); }
+};
+struct SharedSrc {
+    const float4 *p;
+    int off;
+    __device__ __forceinline__ float4 operator()(unsigned j) const { return p[(int)j - off]; }
+};
+
+// Largest cell (in atoms) whose records are staged in shared memory.
+constexpr int RC_STAGE_MAX_ATOMS = 12800;  // 200 KB of float4
+constexpr unsigned RC_STAGE_CHUNK = 32768;  // bytes per bulk copy
+constexpr int RC_SPIN_LIMIT = 1 << 22;
+
+// Copy n float4 records (16-byte aligned) from global memory into shared memory
+// with TMA bulk copies that complete on one mbarrier; every thread waits with a
+// bounded spin.  On a timeout the cell is flagged RC_ETIMEOUT and false returned.
+__device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, int n, int *status, int c) {
+    __shared__ __align__(8) unsigned long long s_bar;
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
+    const unsigned bytes = (unsigned)n * 16u;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const unsigned d0 = (unsigned)__cvta_generic_to_shared(dst);
+        for (unsigned o = 0; o < bytes; o += RC_STAGE_CHUNK) {
+            const unsigned sz = min(RC_STAGE_CHUNK, bytes - o);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d0 + o),
+                "l"(reinterpret_cast<const char *>(src) + o), "r"(sz), "r"(bar)
+                : "memory");
+        }
+    }
+    unsigned done = 0;
+    for (int it = 0; it < RC_SPIN_LIMIT && !done; it++)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    // the whole block agrees, so that either every thread goes on or every thread leaves
+    if (__syncthreads_and(done)) return true;
+    if (threadIdx.x == 0) rc_set_status(status, c, RC_ETIMEOUT);
+    for (int it = 0; it < RC_SPIN_LIMIT && !done; it++)  // let a late copy land before leaving
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    __syncthreads();
+    return false;
+}
+
 // Walk one atom's Verlet list (this lane's share: groups sub, sub+TPA, ... of
 // four entries).  Each group is one 16-byte load; the next group is requested
-// before the current one is processed, and the four neighbour positions of a
-// group are gathered before any pair is evaluated, so several memory requests
+// before the current one is processed, and the four neighbour records of a
+// group are fetched before any pair is evaluated, so several memory requests
 // are in flight per thread.  fn(xj, d) receives the neighbour's record and the
 // exact periodic displacement d = x_j(image) - x_i.
-template <int TPA, class Fn>
-__device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub,
-                                                  const float4 *__restrict__ XG, const float4 &xi, const ShiftTab &T,
-                                                  Fn &&fn) {
+template <int TPA, class Src, class Fn>
+__device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub, const Src &src,
+                                                  const float4 &xi, const ShiftTab &T, Fn &&fn) {
     const int ng = (nn + 3) >> 2;
     int g = sub;
     if (g >= ng) return;
@@ -48,10 +107,10 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
         if (gn < ng) en = __ldg(nb4 + (size_t)gn * RC_TILE);
         const int left = nn - 4 * g;
         if (left >= 4) {
-            const float4 x0 = __ldg(XG + ((unsigned)e.x & RC_IDX_MASK));
-            const float4 x1 = __ldg(XG + ((unsigned)e.y & RC_IDX_MASK));
-            const float4 x2 = __ldg(XG + ((unsigned)e.z & RC_IDX_MASK));
-            const float4 x3 = __ldg(XG + ((unsigned)e.w & RC_IDX_MASK));
+            const float4 x0 = src((unsigned)e.x & RC_IDX_MASK);
+            const float4 x1 = src((unsigned)e.y & RC_IDX_MASK);
+            const float4 x2 = src((unsigned)e.z & RC_IDX_MASK);
+            const float4 x3 = src((unsigned)e.w & RC_IDX_MASK);
             fn(x0, rc_disp(xi, x0, T, (unsigned)e.x >> RC_IDX_BITS));
             fn(x1, rc_disp(xi, x1, T, (unsigned)e.y >> RC_IDX_BITS));
             fn(x2, rc_disp(xi, x2, T, (unsigned)e.z >> RC_IDX_BITS));
@@ -61,7 +120,7 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
 #pragma unroll
             for (int u = 0; u < 3; u++)
                 if (u < left) {
-                    const float4 xj = __ldg(XG + (ee[u] & RC_IDX_MASK));
+                    const float4 xj = src(ee[u] & RC_IDX_MASK);
                     fn(xj, rc_disp(xi, xj, T, ee[u] >> RC_IDX_BITS));
                 }
         }
@@ -73,8 +132,9 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
 
 // Sutton-Chen density pass: rho_i = sum_j (a/r_ij)^m over r < rc; writes
 // xr_i = {x_i, rho_i^{-1/2}} for the force pass.
-template <int TPA, bool M6>
+template <int TPA, bool M6, bool STG>
 __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, int cur) {
+    extern __shared__ __align__(16) float4 s_cell[];
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
@@ -86,6 +146,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
     const float4 *__restrict__ X = cur ? a.x1 : a.x0;
+    if (STG && !stage_records(s_cell, X + off, n, a.status, c)) return;
     const bool live = li < n;
     const int g = off + li;
     float rho = 0.0f;
@@ -96,13 +157,15 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
         const int4 *__restrict__ nb = reinterpret_cast<const int4 *>(a.nbr) + (size_t)t * (p.max_nb / 4) * RC_TILE + at;
         const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m;
         const float rc2 = p.rc2;
-        for_each_neighbor<TPA>(nb, nn, sub, X, xi, s_tab, [&](const float4 &, const float3 &d) {
+        auto body = [&](const float4 &, const float3 &d) {
             const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
             if (r2 < rc2) {
                 const float ar2 = a2 * __fdividef(1.0f, r2);
                 rho += M6 ? ar2 * ar2 * ar2 : powf(ar2, hm);
             }
-        });
+        };
+        if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
+        else for_each_neighbor<TPA>(nb, nn, sub, GlobalSrc{X}, xi, s_tab, body);
     }
     rho = sub_sum<TPA>(rho);
     if (live && sub == 0) a.xr[g] = make_float4(xi.x, xi.y, xi.z, rho > 0.0f ? rsqrtf(rho) : 0.0f);
@@ -130,9 +193,10 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
     }
 }
 
-template <int POT, int TPA, bool M6>
+template <int POT, int TPA, bool M6, bool STG>
 __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, int cur, int mode, int slot,
                                                        int step_index) {
+    extern __shared__ __align__(16) float4 s_cell[];
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
@@ -147,6 +211,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
     const int g = off + li;
     const float4 *__restrict__ X = cur ? a.x1 : a.x0;
     const float4 *__restrict__ XG = (POT == RC_POT_SC) ? a.xr : X;  // gathered array
+    if (STG && !stage_records(s_cell, XG + off, n, a.status, c)) return;
 
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;  // xx yy zz xy xz yz
@@ -160,7 +225,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
             const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m, hn = 0.5f * p.sc_n;
             const float cm2 = 0.5f * p.sc_c * p.sc_m;
             const float rc2 = p.rc2, eps = p.eps, sc_n = p.sc_n, sig = p.sigma;
-            for_each_neighbor<TPA>(nb, nn, sub, XG, xi, s_tab, [&](const float4 &xj, const float3 &d) {
+            auto body = [&](const float4 &xj, const float3 &d) {
                 const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (r2 < rc2) {
@@ -188,12 +253,14 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
                     w5 = fmaf(hy, dz, w5);
                     pe = fmaf(0.5f * eps, arn, pe);
                 }
-            });
+            };
+            if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
+            else for_each_neighbor<TPA>(nb, nn, sub, GlobalSrc{XG}, xi, s_tab, body);
         } else {
             const float s2 = p.sigma * p.sigma;
             const float c24 = 24.0f * p.eps, c2 = 2.0f * p.eps;
             const float rc2 = p.rc2;
-            for_each_neighbor<TPA>(nb, nn, sub, XG, xi, s_tab, [&](const float4 &, const float3 &d) {
+            auto body = [&](const float4 &, const float3 &d) {
                 const float dx = d.x, dy = d.y, dz = d.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if (r2 < rc2) {
@@ -214,7 +281,9 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
                     w5 = fmaf(hy, dz, w5);
                     pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
                 }
-            });
+            };
+            if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
+            else for_each_neighbor<TPA>(nb, nn, sub, GlobalSrc{XG}, xi, s_tab, body);
         }
     }
     fx = sub_sum<TPA>(fx);
@@ -240,7 +309,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
 #pragma unroll
         for (int b = 0; b < RC_MAX_BONDS; b++) {
             if (q[b] < 0) continue;
-            const float4 xj = X[off + q[b]];
+            const float4 xj = STG ? s_cell[q[b]] : X[off + q[b]];
             // minimum image: pick the integer shift from fractional coordinates, then
             // form the displacement through the exact shift table
             const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
@@ -345,43 +414,92 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, in
     }
 }
 
-template <int POT, bool M6>
+template <class K>
+void set_smem(K kernel, int bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int POT, bool M6, bool STG>
 void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
-                      int step_index, cudaStream_t s) {
+                      int step_index, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: k_force<POT, 1, M6><<<n_tiles, RC_TILE * 1, 0, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 2: k_force<POT, 2, M6><<<n_tiles, RC_TILE * 2, 0, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 4: k_force<POT, 4, M6><<<n_tiles, RC_TILE * 4, 0, s>>>(p, a, cur, mode, slot, step_index); break;
-    default: k_force<POT, 8, M6><<<n_tiles, RC_TILE * 8, 0, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 1: k_force<POT, 1, M6, STG><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 2: k_force<POT, 2, M6, STG><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 4: k_force<POT, 4, M6, STG><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    default: k_force<POT, 8, M6, STG><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur, mode, slot, step_index); break;
     }
 }
 
-template <bool M6>
-void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s) {
+template <bool M6, bool STG>
+void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: k_density<1, M6><<<n_tiles, RC_TILE * 1, 0, s>>>(p, a, cur); break;
-    case 2: k_density<2, M6><<<n_tiles, RC_TILE * 2, 0, s>>>(p, a, cur); break;
-    case 4: k_density<4, M6><<<n_tiles, RC_TILE * 4, 0, s>>>(p, a, cur); break;
-    default: k_density<8, M6><<<n_tiles, RC_TILE * 8, 0, s>>>(p, a, cur); break;
+    case 1: k_density<1, M6, STG><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur); break;
+    case 2: k_density<2, M6, STG><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur); break;
+    case 4: k_density<4, M6, STG><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur); break;
+    default: k_density<8, M6, STG><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur); break;
     }
+}
+
+template <int POT, bool M6>
+void prepare_pot(int bytes) {
+    set_smem(k_force<POT, 1, M6, true>, bytes);
+    set_smem(k_force<POT, 2, M6, true>, bytes);
+    set_smem(k_force<POT, 4, M6, true>, bytes);
+    set_smem(k_force<POT, 8, M6, true>, bytes);
+}
+
+template <bool M6>
+void prepare_density(int bytes) {
+    set_smem(k_density<1, M6, true>, bytes);
+    set_smem(k_density<2, M6, true>, bytes);
+    set_smem(k_density<4, M6, true>, bytes);
+    set_smem(k_density<8, M6, true>, bytes);
 }
 
 }  // namespace
 
-void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s) {
-    if (p.sc_m == 6.0f) launch_density_m<true>(p, a, cur, n_tiles, tpa, s);
-    else launch_density_m<false>(p, a, cur, n_tiles, tpa, s);
+int rc_stage_max_atoms() { return RC_STAGE_MAX_ATOMS; }
+
+void rc_prepare_staged(int max_cell_atoms) {
+    const int bytes = max_cell_atoms * 16;
+    prepare_pot<RC_POT_SC, true>(bytes);
+    prepare_pot<RC_POT_SC, false>(bytes);
+    prepare_pot<RC_POT_LJ, false>(bytes);
+    prepare_pot<RC_POT_KG, false>(bytes);
+    prepare_density<true>(bytes);
+    prepare_density<false>(bytes);
+}
+
+void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int stage_atoms,
+                       cudaStream_t s) {
+    const int smem = stage_atoms * 16;
+    if (stage_atoms > 0) {
+        if (p.sc_m == 6.0f) launch_density_m<true, true>(p, a, cur, n_tiles, tpa, smem, s);
+        else launch_density_m<false, true>(p, a, cur, n_tiles, tpa, smem, s);
+    } else {
+        if (p.sc_m == 6.0f) launch_density_m<true, false>(p, a, cur, n_tiles, tpa, 0, s);
+        else launch_density_m<false, false>(p, a, cur, n_tiles, tpa, 0, s);
+    }
 }
 
 void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
-                     int step_index, cudaStream_t s) {
+                     int step_index, int stage_atoms, cudaStream_t s) {
     const bool m69 = p.sc_m == 6.0f && p.sc_n == 9.0f;
+    const int smem = stage_atoms * 16;
+    const bool st = stage_atoms > 0;
     if (p.pot == RC_POT_SC) {
-        if (m69) launch_force_pot<RC_POT_SC, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
-        else launch_force_pot<RC_POT_SC, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+        if (m69) {
+            if (st) launch_force_pot<RC_POT_SC, true, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
+            else launch_force_pot<RC_POT_SC, true, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, 0, s);
+        } else {
+            if (st) launch_force_pot<RC_POT_SC, false, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
+            else launch_force_pot<RC_POT_SC, false, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, 0, s);
+        }
     } else if (p.pot == RC_POT_KG) {
-        launch_force_pot<RC_POT_KG, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+        if (st) launch_force_pot<RC_POT_KG, false, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
+        else launch_force_pot<RC_POT_KG, false, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, 0, s);
     } else {
-        launch_force_pot<RC_POT_LJ, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, s);
+        if (st) launch_force_pot<RC_POT_LJ, false, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
+        else launch_force_pot<RC_POT_LJ, false, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, 0, s);
     }
 }

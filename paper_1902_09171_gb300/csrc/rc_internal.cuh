@@ -153,9 +153,14 @@ __device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, co
 // host-side launchers (defined in the kernel translation units)
 void rc_launch_sort(const KParams &p, const KArrays &a, int cur, int n_cells, cudaStream_t s);
 void rc_launch_nlist(const KParams &p, const KArrays &a, int cur, int n_tiles, cudaStream_t s);
-void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, cudaStream_t s);
+// stage_atoms > 0: every CTA first copies its whole r-cell (stage_atoms = the
+// largest cell of the batch) into shared memory and gathers neighbours there
+void rc_launch_density(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int stage_atoms,
+                       cudaStream_t s);
 void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
-                     int step_index, cudaStream_t s);
+                     int step_index, int stage_atoms, cudaStream_t s);
+int rc_stage_max_atoms();
+void rc_prepare_staged(int max_cell_atoms);
 void rc_launch_deform_impl(const double *F, double *H, double *Rprev, double *Q, double *R, double *Fst, double *dR,
                            const double *H0, float *Hf, float *Hif, int *status, int *need_rebuild, int *nbins,
                            const int *bin_cap, const int *active, double rlist, int n_cells, cudaStream_t s);

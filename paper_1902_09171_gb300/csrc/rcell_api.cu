@@ -48,6 +48,8 @@ struct rcell_ctx {
     int cur = 0;
     int tpa = 1;
     int use_graphs = 1;
+    int max_cell = 0;    // largest cell of the batch (atoms)
+    int staged = 1;      // stage whole cells in shared memory when they fit
     long launches_last = 0;
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, int, int, int>, long> graph_launches;
@@ -114,6 +116,10 @@ int first_status(rcell_ctx *c) {
     return RC_OK;
 }
 
+int stage_atoms(const rcell_ctx *c) {
+    return (c->staged && c->max_cell <= rc_stage_max_atoms()) ? c->max_cell : 0;
+}
+
 // enqueue the neighbour rebuild (when scheduled) and the force launches of one
 // step; returns the number of kernels enqueued
 long enqueue_step(rcell_ctx *c, int mode, int slot, int step_index) {
@@ -122,10 +128,10 @@ long enqueue_step(rcell_ctx *c, int mode, int slot, int step_index) {
     rc_launch_nlist(c->kp, c->ka, c->cur, c->n_tiles, c->stream);
     k += 2;
     if (c->kp.pot == RC_POT_SC) {
-        rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, c->stream);
+        rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, stage_atoms(c), c->stream);
         k++;
     }
-    rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, slot, step_index, c->stream);
+    rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, slot, step_index, stage_atoms(c), c->stream);
     k++;
     return k;
 }
@@ -206,6 +212,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
         if (!(V > 0)) { rcell_destroy(c); return RC_EINVAL; }
         rho_max = std::max(rho_max, ci.n_atoms / V);
         c->h_n[i] = ci.n_atoms;
+        c->max_cell = std::max(c->max_cell, ci.n_atoms);
         c->h_ntiles[i] = (ci.n_atoms + RC_TILE - 1) / RC_TILE;
         c->h_tile0[i] = (int)tiles;
         c->h_off[i] = (int)(tiles * RC_TILE);
@@ -230,6 +237,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     int max_nb = (int)std::ceil(1.6 * est + 32);
     max_nb = (max_nb + 7) / 8 * 8;
 
+    if (c->max_cell <= rc_stage_max_atoms()) rc_prepare_staged(c->max_cell);
     // ---- kernel parameters ----
     KParams &kp = c->kp;
     const double ftm2v = ftm2v_of(P.units);
@@ -575,11 +583,21 @@ int rcell_clear_status(rcell_ctx *c) {
     return RC_OK;
 }
 
+int rcell_set_staging(rcell_ctx *c, int staged) {
+    if (!c) return RC_EINVAL;
+    if (staged >= 0 && (staged ? 1 : 0) != c->staged) {
+        c->staged = staged ? 1 : 0;
+        free_graphs(c);
+    }
+    return RC_OK;
+}
+
 int rcell_set_tuning(rcell_ctx *c, int threads_per_atom, int use_graphs) {
     if (!c) return RC_EINVAL;
     if (threads_per_atom >= 0) {
         if (threads_per_atom != 1 && threads_per_atom != 2 && threads_per_atom != 4 && threads_per_atom != 8)
             return fail(c, RC_EINVAL, "threads_per_atom must be 1, 2, 4 or 8");
+        if (threads_per_atom != c->tpa) free_graphs(c);
         c->tpa = threads_per_atom;
     }
     if (use_graphs >= 0) c->use_graphs = use_graphs ? 1 : 0;
@@ -694,9 +712,9 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
         CKC(c, cudaEventRecord(ev[1], c->stream));
         rc_launch_nlist(c->kp, c->ka, c->cur, c->n_tiles, c->stream);
         CKC(c, cudaEventRecord(ev[2], c->stream));
-        if (c->kp.pot == RC_POT_SC) rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, c->stream);
+        if (c->kp.pot == RC_POT_SC) rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, stage_atoms(c), c->stream);
         CKC(c, cudaEventRecord(ev[3], c->stream));
-        rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, -1, s, c->stream);
+        rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, -1, s, stage_atoms(c), c->stream);
         CKC(c, cudaEventRecord(ev[4], c->stream));
         CKC(c, cudaEventSynchronize(ev[4]));
         lap(0, 1, 0);

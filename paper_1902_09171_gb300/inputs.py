@@ -199,14 +199,17 @@ def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
 
 
 def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, max_shear: float = 0.08,
-                 jitter: float = 0.01):
-    """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I):
-    a mix of monotone and cyclic uniaxial stretch along x (amplitude up to
-    max_strain in tension, half of it in compression), lateral strain
-    -nu * eps_x with nu drawn in [0, 0.5], a monotone simple shear F_xy up to
-    max_shear, plus a small random ramp (amplitude `jitter`) in all nine
-    components so that every input component is exercised.
-    Returns an (n_paths, n_inc + 1, 3, 3) array."""
+                 jitter: float = 0.01, max_lateral: float = 0.2):
+    """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I).
+
+    Axial stretch along x: monotone or cyclic, amplitude up to max_strain in
+    tension and half of it in compression.  Each lateral stretch (y, z) is
+    -nu * eps_x (nu in [0, 0.5]) plus its own drift that saturates on a random
+    time scale (from a few increments to the whole path), between -max_lateral
+    and +max_lateral / 4 -- so paths include lateral contraction at zero axial
+    load, as a free surface under residual tension produces.  A monotone simple
+    shear F_xy up to max_shear and a small random ramp (amplitude `jitter`) in
+    all nine components complete the path.  Returns (n_paths, n_inc + 1, 3, 3)."""
     rng = np.random.default_rng(seed)
     t = np.arange(n_inc + 1) / n_inc
     F = np.tile(np.eye(3), (n_paths, n_inc + 1, 1, 1))
@@ -220,8 +223,10 @@ def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, m
         nu = rng.uniform(0.0, 0.5)
         gam = rng.uniform(-max_shear, max_shear) * t
         F[p, :, 0, 0] = 1.0 + ex
-        F[p, :, 1, 1] = 1.0 - nu * ex
-        F[p, :, 2, 2] = 1.0 - nu * ex
+        for d in (1, 2):
+            drift = rng.uniform(-max_lateral, 0.25 * max_lateral)
+            tau = np.exp(rng.uniform(np.log(2.0 / n_inc), 0.0))
+            F[p, :, d, d] = 1.0 - nu * ex + drift * (1.0 - np.exp(-t / tau)) / (1.0 - np.exp(-1.0 / tau))
         F[p, :, 0, 1] = gam
         F[p] += jitter * rng.uniform(-1, 1, (3, 3))[None] * t[:, None, None]
     return F

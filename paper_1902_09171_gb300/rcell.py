@@ -47,7 +47,7 @@ class rcell_init(C.Structure):
 _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
-           "rcell_clear_status", "rcell_set_active", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
+           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
            "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
@@ -76,6 +76,7 @@ def load(path: str | None = None):
         "rcell_sync": ([vp], C.c_int),
         "rcell_clear_status": ([vp], C.c_int),
         "rcell_set_active": ([vp, vp, C.c_int], C.c_int),
+        "rcell_set_staging": ([vp, C.c_int], C.c_int),
         "rcell_set_tuning": ([vp, C.c_int, C.c_int], C.c_int),
         "rcell_info": ([vp, I, C.POINTER(C.c_long), C.POINTER(C.c_long)], C.c_int),
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
@@ -249,6 +250,10 @@ def rcell_set_active(ctx, mask):
         keep = np.ascontiguousarray(mask, dtype=np.int32)
         p, where = C.c_void_p(keep.ctypes.data), RC_HOST
     _check(load().rcell_set_active(ctx, p, where), ctx, "rcell_set_active")
+
+
+def rcell_set_staging(ctx, staged: int):
+    _check(load().rcell_set_staging(ctx, int(staged)), ctx, "rcell_set_staging")
 
 
 def rcell_set_tuning(ctx, threads_per_atom: int = -1, use_graphs: int = -1):
