@@ -199,7 +199,7 @@ def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
 
 
 def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, max_shear: float = 0.08,
-                 jitter: float = 0.01, max_lateral: float = 0.2):
+                 jitter: float = 0.01, max_lateral: float = 0.1):
     """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I).
 
     Axial stretch along x: monotone or cyclic, amplitude up to max_strain in
