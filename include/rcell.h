@@ -188,9 +188,11 @@ int rcell_clear_status(rcell_ctx *ctx);
  *   use_graphs       : 0/1, capture rcell_run into CUDA graphs */
 int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
 
-/* Shared-memory staging of whole r-cells (1, the default: on for batches whose
- * largest cell has at most 12800 atoms; 0: neighbours are gathered from global
- * memory).  Both give the same results up to summation order. */
+/* Shared-memory staging of whole r-cells: with 1, every CTA first copies its
+ * r-cell's records into shared memory (TMA bulk copy) and gathers neighbours
+ * there -- only for batches whose largest cell has at most 12800 atoms; with 0
+ * (the default) neighbours are gathered from global memory through the
+ * read-only cache.  Both give the same results up to summation order. */
 int rcell_set_staging(rcell_ctx *ctx, int staged);
 
 /* Number of cells, total atoms, and the number of kernels the last rcell_run

@@ -49,7 +49,7 @@ struct rcell_ctx {
     int tpa = 1;
     int use_graphs = 1;
     int max_cell = 0;    // largest cell of the batch (atoms)
-    int staged = 1;      // stage whole cells in shared memory when they fit
+    int staged = 0;      // stage whole cells in shared memory (when they fit) -- off by default
     long launches_last = 0;
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, int, int, int>, long> graph_launches;

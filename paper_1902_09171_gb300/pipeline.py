@@ -131,6 +131,34 @@ def relative_error(sur, U, Y, n_members, s_floor=0.0, with_spread=False):
     return err, [float(v) for v in q]
 
 
+def fe_compare_surrogate_only(ctx_sg, sur, fe_sg, n_members, lambdas, n_steps, n_avg, spread_on, spread_off, s_floor,
+                              reference, md_first=2, stream=None):
+    """The surrogate half of fe_compare against a stored all-MD reference
+    (axial stress curve, milliseconds)."""
+    torch = _torch()
+    ne = rcell.rcell_info(ctx_sg)[0]
+    dev = torch.device("cuda")
+    st = stream or torch.cuda.current_stream()
+    h = torch.zeros((n_members, ne, 128), dtype=torch.float32, device=dev)
+    Fp = torch.eye(3, dtype=torch.float64, device=dev).repeat(ne, 1, 1).contiguous()
+    flag = torch.zeros(ne, dtype=torch.int32, device=dev)
+    P = torch.zeros((ne, 3, 3), dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P_sg, n_md = [], []
+    e0.record(st)
+    for k, lam in enumerate(lambdas):
+        n_md.append(rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
+                                            k < md_first, h, Fp, flag))
+        rcell.fe_get_P(fe_sg, P)
+        P_sg.append(P[:, 0, 0].mean())
+    e1.record(st)
+    torch.cuda.synchronize()
+    a, b = np.array(reference[0]), np.array([float(v) for v in P_sg])
+    return {"ms_sg": e0.elapsed_time(e1), "axial_sg": b.tolist(), "n_md": n_md,
+            "max_rel_dev": float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30)),
+            "md_fraction": float(sum(n_md) / (ne * len(lambdas)))}
+
+
 def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n_avg, spread_on=0.02,
                spread_off=0.01, s_floor=0.05, md_first=2, stream=None):
     """Drive two identical FE bars through the same load history: one with all
