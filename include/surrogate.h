@@ -82,6 +82,17 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
  * `stream`. */
 int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream);
 
+/* GEMM engine for the forward and data-gradient products: 0 = warp-level BF16
+ * tensor-core instructions (mma.sync, the default), 1 = 5th-generation tensor
+ * cores (tcgen05: operands in shared memory, FP32 accumulator in tensor
+ * memory).  Weight gradients always use the first.  Same results up to
+ * summation order. */
+int sur_set_backend(sur_ctx *s, int backend);
+
+/* Wait for the stream; return RC_ETIMEOUT if a bounded tensor-core wait gave up,
+ * else RC_OK. */
+int sur_sync(sur_ctx *s);
+
 /* Number of members and the stream of a surrogate context (either may be NULL). */
 int sur_info(const sur_ctx *s, int *n_members, void **stream);
 

@@ -179,6 +179,153 @@ void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *
 }
 
 // ---------------------------------------------------------------------------
+// The same GEMM on the 5th-generation tensor cores (tcgen05): C[M x N] =
+// A[M x K] * Bk[N x K]^T with both operands K-major.  One CTA computes a
+// 128 x 64 tile with the whole K (<= 256) resident in shared memory:
+//   * operands are written to shared memory in the K-major "core matrix"
+//     layout (8 rows x 16 bytes per core matrix, no swizzle): core (r/8, k/8)
+//     at byte (k/8 * rows/8 + r/8) * 128, row r%8 at +16 (r%8);
+//   * one elected thread issues K/16 tcgen05.mma (kind::f16, BF16 inputs,
+//     FP32 accumulator in tensor memory) and a tcgen05.commit onto an mbarrier;
+//   * every warp waits on the mbarrier (bounded), reads its 32 accumulator rows
+//     with tcgen05.ld and runs the fused epilogue; tensor memory is freed on
+//     every path.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 64, TC_THREADS = 128, TC_SPIN = 1 << 22;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores; no swizzle
+    return d;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                          const __nv_bfloat16 *__restrict__ Bk, int ldb, int M, int N,
+                                                          int K, Epi e, int *err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+    const int KC = K >> 3;  // 16-byte chunks along K
+    unsigned char *sA = tc_smem, *sB = tc_smem + (size_t)TC_M * K * 2;
+    // tensor memory: 64 columns x 128 lanes of FP32 for the 128 x 64 accumulator
+    if (warp == 0) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // operands into the core-matrix layout
+    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    for (int idx = tid; idx < TC_M * KC; idx += TC_THREADS) {
+        const int r = idx / KC, kc = idx - r * KC;
+        uint4 v = z4;
+        if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + kc * 8);
+        *reinterpret_cast<uint4 *>(sA + ((size_t)kc * (TC_M / 8) + (r >> 3)) * 128 + (r & 7) * 16) = v;
+    }
+    for (int idx = tid; idx < TC_N * KC; idx += TC_THREADS) {
+        const int r = idx / KC, kc = idx - r * KC;
+        uint4 v = z4;
+        if (n0 + r < N) v = *reinterpret_cast<const uint4 *>(Bk + (size_t)(n0 + r) * ldb + kc * 8);
+        *reinterpret_cast<uint4 *>(sB + ((size_t)kc * (TC_N / 8) + (r >> 3)) * 128 + (r & 7) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    if (tid == 0) {
+        // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N/8, M/16
+        const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                               ((unsigned)(TC_M >> 4) << 24);
+        const unsigned a0 = (unsigned)__cvta_generic_to_shared(sA), b0 = (unsigned)__cvta_generic_to_shared(sB);
+        const unsigned lboA = (TC_M / 8) * 128, lboB = (TC_N / 8) * 128;
+        for (int kk = 0; kk < (K >> 4); kk++) {
+            const uint64_t ad = tc_desc(a0 + kk * 2 * lboA, lboA, 128);
+            const uint64_t bd = tc_desc(b0 + kk * 2 * lboB, lboB, 128);
+            const unsigned acc = kk > 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    }
+    unsigned done = 0;
+    for (int it = 0; it < TC_SPIN && !done; it++)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    const int ok = __syncthreads_and(done);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            unsigned r[16];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j++) epilogue<EPI>(e, row, n0 + c0 + j, M, N, __uint_as_float(r[j]));
+        }
+    } else if (tid == 0) {
+        atomicExch(err, RC_ETIMEOUT);
+        // let the tensor-core work in flight finish before its memory is released
+        for (int it = 0; it < TC_SPIN && !done; it++)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+// C = A[M x K] * Bk[N x K]^T on tcgen05 (K a multiple of 16, K <= 256)
+template <int EPI>
+void gemm_tc05(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bk, int ldb, int M, int N, int K,
+               const Epi &e, int *err) {
+    dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M);
+    const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
+    k_gemm_tc05<EPI><<<grid, TC_THREADS, smem, s>>>(A, lda, Bk, ldb, M, N, K, e, err);
+}
+
+void prepare_tc05() {
+    const int bytes = (TC_M + TC_N) * 256 * 2;
+    cudaFuncSetAttribute(k_gemm_tc05<EPI_GELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_gemm_tc05<EPI_HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_gemm_tc05<EPI_DGELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_gemm_tc05<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
 
@@ -317,6 +464,8 @@ struct sur_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int K = 0, Bmax = 0, Tmax = 0;
+    int backend = 0;  // 0: mma.sync kernels, 1: tcgen05 kernels for the forward and data-gradient GEMMs
+    int *d_err = nullptr;
     std::vector<SurMember> mem;
     std::vector<void *> allocs;
     float *u_inv = nullptr, *s_inv = nullptr, *s_mul = nullptr;
@@ -363,7 +512,8 @@ void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, c
             e.bias = M.theta + BOFF[l];
             e.y_out = Ys[l] + (size_t)t * RB * WID;
             e.a_out = As_[l] + (size_t)t * RB * WID;
-            gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, B, WID, kin, e);
+            if (s->backend) gemm_tc05<EPI_GELU>(s->stream, in, kin, M.Wt[l], kin, B, WID, kin, e, s->d_err);
+            else gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, B, WID, kin, e);
             in = e.a_out;
             kin = WID;
         }
@@ -374,7 +524,8 @@ void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, c
         h.s_mul = s_mul;  // null during training: the loss works in network units
         h.h_next = (t + 1 < T) ? s->Z + (size_t)(t + 1) * RB * K0 : nullptr;
         h.h_f32 = nullptr;
-        gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, B, N4, WID, h);
+        if (s->backend) gemm_tc05<EPI_HEAD>(s->stream, in, WID, M.Wt[3], WID, B, N4, WID, h, s->d_err);
+        else gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, B, N4, WID, h);
     }
 }
 
@@ -394,18 +545,22 @@ void backward(sur_ctx *s, SurMember &M, const float *Y, int B, int T, const floa
         // dY3 = (dO W4^T) * gelu'(Y3)
         e.y_in = s->Y3 + (size_t)t * RB * WID;
         e.a_out = s->dY3 + (size_t)t * RB * WID;
-        gemm<EPI_DGELU, false>(s->stream, dOt, N4, M.Wt[3], WID, B, WID, N4, e);
+        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, dOt, N4, M.W[3], N4, B, WID, N4, e, s->d_err);
+        else gemm<EPI_DGELU, false>(s->stream, dOt, N4, M.Wt[3], WID, B, WID, N4, e);
         e.y_in = s->Y2 + (size_t)t * RB * WID;
         e.a_out = s->dY2 + (size_t)t * RB * WID;
-        gemm<EPI_DGELU, false>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.Wt[2], WID, B, WID, WID, e);
+        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.W[2], WID, B, WID, WID, e, s->d_err);
+        else gemm<EPI_DGELU, false>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.Wt[2], WID, B, WID, WID, e);
         e.y_in = s->Y1 + (size_t)t * RB * WID;
         e.a_out = s->dY1 + (size_t)t * RB * WID;
-        gemm<EPI_DGELU, false>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.Wt[1], WID, B, WID, WID, e);
+        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.W[1], WID, B, WID, WID, e, s->d_err);
+        else gemm<EPI_DGELU, false>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.Wt[1], WID, B, WID, WID, e);
         if (t > 0) {  // dZ = dY1 W1^T (only the state part is used by step t-1)
             Epi f{};
             f.s_out = s->dZ;
             f.s_ld = K0;
-            gemm<EPI_F32, false>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.Wt[0], K0, B, K0, WID, f);
+            if (s->backend) gemm_tc05<EPI_F32>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.W[0], WID, B, K0, WID, f, s->d_err);
+            else gemm<EPI_F32, false>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.Wt[0], K0, B, K0, WID, f);
         }
     }
     // weight gradients over all steps at once: dW = op(A_all)^T dY_all (split-K)
@@ -482,6 +637,8 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
     ok &= salloc(s, &s->Sm, (size_t)max_batch * NOUT * n_members) == cudaSuccess;
     ok &= salloc(s, &s->dZ, (size_t)max_batch * K0) == cudaSuccess;
     ok &= salloc(s, &s->loss_acc, 1) == cudaSuccess;
+    ok &= salloc(s, &s->d_err, 1) == cudaSuccess;
+    prepare_tc05();
     s->mem.resize(n_members);
     for (auto &M : s->mem) {
         ok &= salloc(s, &M.theta, NPAR) == cudaSuccess;
@@ -611,7 +768,8 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
             e.bias = M.theta + BOFF[l];
             e.y_out = Ys[l];
             e.a_out = As_[l];
-            gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, n, WID, kin, e);
+            if (s->backend) gemm_tc05<EPI_GELU>(s->stream, in, kin, M.Wt[l], kin, n, WID, kin, e, s->d_err);
+            else gemm<EPI_GELU, false>(s->stream, in, kin, M.W[l], WID, n, WID, kin, e);
             in = As_[l];
             kin = WID;
         }
@@ -622,10 +780,25 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
         hd.s_mul = s->s_mul;
         hd.h_next = nullptr;
         hd.h_f32 = hk;  // the new state replaces the old one (the input row holds a BF16 copy)
-        gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, n, N4, WID, hd);
+        if (s->backend) gemm_tc05<EPI_HEAD>(s->stream, in, WID, M.Wt[3], WID, n, N4, WID, hd, s->d_err);
+        else gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, n, N4, WID, hd);
     }
     k_ensemble<<<cdiv(n, 128), 128, 0, s->stream>>>(s->Sm, s->K, n, s_floor, s_mean, spread);
     return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_set_backend(sur_ctx *s, int backend) {
+    if (!s || backend < 0 || backend > 1) return RC_EINVAL;
+    s->backend = backend;
+    return RC_OK;
+}
+
+int sur_sync(sur_ctx *s) {
+    if (!s) return RC_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return RC_ECUDA;
+    int e = 0;
+    if (cudaMemcpy(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RC_ECUDA;
+    return e;
 }
 
 int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream) {

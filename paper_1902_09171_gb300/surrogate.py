@@ -14,7 +14,7 @@ from . import rcell
 SUR_N_IN, SUR_N_H, SUR_N_OUT, SUR_WIDTH = 15, 128, 6, 256
 SUR_N_PARAMS = 144 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 144 + 144
 EXPORTS = ["sur_create", "sur_set_scaling", "sur_get_params", "sur_set_params", "sur_loss_grad", "sur_train_step",
-           "sur_predict", "sur_step", "sur_features", "sur_info", "sur_destroy"]
+           "sur_predict", "sur_step", "sur_features", "sur_set_backend", "sur_sync", "sur_info", "sur_destroy"]
 _bound = False
 
 
@@ -34,6 +34,8 @@ def _lib():
             "sur_step": ([vp, vp, C.c_int, vp, C.c_float, vp, vp], C.c_int),
             "sur_features": ([vp, vp, C.c_int, vp, vp], C.c_int),
             "sur_info": ([vp, C.POINTER(C.c_int), C.POINTER(vp)], C.c_int),
+            "sur_set_backend": ([vp, C.c_int], C.c_int),
+            "sur_sync": ([vp], C.c_int),
             "sur_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
@@ -110,6 +112,14 @@ def sur_step(s, u, h, s_floor, s_mean, spread):
 def sur_features(F_prev, F, u, stream=None):
     """F_prev, F: CUDA float64 (n, 3, 3); u: CUDA float32 (n, 15) output."""
     _chk(_lib().sur_features(_dp(F_prev), _dp(F), int(F.shape[0]), _dp(u), rcell._stream_ptr(stream)), "sur_features")
+
+
+def sur_set_backend(s, backend):
+    _chk(_lib().sur_set_backend(s, int(backend)), "sur_set_backend")
+
+
+def sur_sync(s):
+    return _lib().sur_sync(s)
 
 
 def sur_info(s):
