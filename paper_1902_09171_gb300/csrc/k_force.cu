@@ -88,45 +88,62 @@ __device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, in
     return false;
 }
 
+// Slots of a list group past the end of the list hold stale data: point them at
+// the group's first entry, which is always valid, so that they can be gathered.
+__device__ __forceinline__ int4 clamp_group(int4 e, int left) {
+    if (left < 4) {
+        if (left < 2) e.y = e.x;
+        if (left < 3) e.z = e.x;
+        e.w = e.x;
+    }
+    return e;
+}
+
 // Walk one atom's Verlet list (this lane's share: groups sub, sub+TPA, ... of
-// four entries).  Each group is one 16-byte load; the next group is requested
-// before the current one is processed, and the four neighbour records of a
-// group are fetched before any pair is evaluated, so several memory requests
-// are in flight per thread.  fn(xj, d) receives the neighbour's record and the
-// exact periodic displacement d = x_j(image) - x_i.
+// four entries).  Each group is one 16-byte load.  The loop is software
+// pipelined: while the pairs of group g are evaluated, the four neighbour
+// records of the next group are already being gathered and the list entries of
+// the group after that are being loaded, so the gather latency overlaps the
+// pair arithmetic.  fn(xj, d) receives the neighbour's record and the exact
+// periodic displacement d = x_j(image) - x_i.
 template <int TPA, class Src, class Fn>
 __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub, const Src &src,
                                                   const float4 &xi, const ShiftTab &T, Fn &&fn) {
     const int ng = (nn + 3) >> 2;
     int g = sub;
     if (g >= ng) return;
-    int4 e = __ldg(nb4 + (size_t)g * RC_TILE);
+    int4 e = clamp_group(__ldg(nb4 + (size_t)g * RC_TILE), nn - 4 * g);
+    float4 c0 = src((unsigned)e.x & RC_IDX_MASK), c1 = src((unsigned)e.y & RC_IDX_MASK);
+    float4 c2 = src((unsigned)e.z & RC_IDX_MASK), c3 = src((unsigned)e.w & RC_IDX_MASK);
+    int gn = g + TPA;
+    int4 en = e;
+    if (gn < ng) en = __ldg(nb4 + (size_t)gn * RC_TILE);
     while (true) {
-        const int gn = g + TPA;
-        int4 en = e;
-        if (gn < ng) en = __ldg(nb4 + (size_t)gn * RC_TILE);
-        const int left = nn - 4 * g;
-        if (left >= 4) {
-            const float4 x0 = src((unsigned)e.x & RC_IDX_MASK);
-            const float4 x1 = src((unsigned)e.y & RC_IDX_MASK);
-            const float4 x2 = src((unsigned)e.z & RC_IDX_MASK);
-            const float4 x3 = src((unsigned)e.w & RC_IDX_MASK);
-            fn(x0, rc_disp(xi, x0, T, (unsigned)e.x >> RC_IDX_BITS));
-            fn(x1, rc_disp(xi, x1, T, (unsigned)e.y >> RC_IDX_BITS));
-            fn(x2, rc_disp(xi, x2, T, (unsigned)e.z >> RC_IDX_BITS));
-            fn(x3, rc_disp(xi, x3, T, (unsigned)e.w >> RC_IDX_BITS));
-        } else {
-            const unsigned ee[3] = {(unsigned)e.x, (unsigned)e.y, (unsigned)e.z};
-#pragma unroll
-            for (int u = 0; u < 3; u++)
-                if (u < left) {
-                    const float4 xj = src(ee[u] & RC_IDX_MASK);
-                    fn(xj, rc_disp(xi, xj, T, ee[u] >> RC_IDX_BITS));
-                }
+        const int gnn = gn + TPA;
+        float4 n0 = c0, n1 = c1, n2 = c2, n3 = c3;
+        int4 enn = en;
+        if (gn < ng) {  // next stage: gather group gn, load the entries of group gnn
+            en = clamp_group(en, nn - 4 * gn);
+            n0 = src((unsigned)en.x & RC_IDX_MASK);
+            n1 = src((unsigned)en.y & RC_IDX_MASK);
+            n2 = src((unsigned)en.z & RC_IDX_MASK);
+            n3 = src((unsigned)en.w & RC_IDX_MASK);
+            if (gnn < ng) enn = __ldg(nb4 + (size_t)gnn * RC_TILE);
         }
+        const int left = nn - 4 * g;
+        fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
+        if (left > 1) fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
+        if (left > 2) fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
+        if (left > 3) fn(c3, rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS));
         if (gn >= ng) break;
-        e = en;
         g = gn;
+        gn = gnn;
+        e = en;
+        en = enn;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
     }
 }
 
@@ -193,8 +210,16 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
     }
 }
 
+// Resident CTAs per SM the force kernel is compiled for at one lane per atom
+// (caps its registers at 65536 / (128 * RC_FORCE_MIN_CTAS)); 1 leaves the
+// register count to the compiler.
+#ifndef RC_FORCE_MIN_CTAS
+#define RC_FORCE_MIN_CTAS 1
+#endif
+constexpr int force_min_ctas(int tpa) { return RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1; }
+
 template <int POT, int TPA, bool M6, bool STG>
-__global__ void __launch_bounds__(RC_TILE *TPA) k_force(KParams p, KArrays a, int cur, int mode, int slot,
+__global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KParams p, KArrays a, int cur, int mode, int slot,
                                                        int step_index) {
     extern __shared__ __align__(16) float4 s_cell[];
     const int t = blockIdx.x;

@@ -121,8 +121,10 @@ __device__ __forceinline__ void rc_set_status(int *status, int cell, int code) {
 // x_j + sn and x_i - sp subtract numbers of similar size (exact), so only the
 // final subtraction rounds -- the result is the correctly rounded displacement
 // instead of one carrying an error of half an ulp of the box length.
+// Per image code: a = {min(sh,0) (3), lo.x}, b = {max(sh,0) (3), lo.y}; the z
+// shift n2 * H_zz is exact in FP32, so lo.z = 0.  Two 16-byte shared loads per pair.
 struct ShiftTab {
-    float4 sn[27], sp[27], lo[27];
+    float4 a[27], b[27];
 };
 
 __device__ __forceinline__ void rc_build_shift(ShiftTab &T, const float *H, int code) {
@@ -131,9 +133,8 @@ __device__ __forceinline__ void rc_build_shift(ShiftTab &T, const float *H, int 
     const double hy = (double)H[3] * sy + (double)H[4] * sz;
     const double hz = (double)H[5] * sz;
     const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
-    T.sn[code] = make_float4(fminf(fx, 0.f), fminf(fy, 0.f), fminf(fz, 0.f), 0.f);
-    T.sp[code] = make_float4(fmaxf(fx, 0.f), fmaxf(fy, 0.f), fmaxf(fz, 0.f), 0.f);
-    T.lo[code] = make_float4((float)(hx - fx), (float)(hy - fy), (float)(hz - fz), 0.f);
+    T.a[code] = make_float4(fminf(fx, 0.f), fminf(fy, 0.f), fminf(fz, 0.f), (float)(hx - fx));
+    T.b[code] = make_float4(fmaxf(fx, 0.f), fmaxf(fy, 0.f), fmaxf(fz, 0.f), (float)(hy - fy));
 }
 
 // fill the table from cell c's box (call with all threads; syncs)
@@ -145,9 +146,9 @@ __device__ __forceinline__ void rc_load_shifts(ShiftTab &T, float *s_H, const fl
 }
 
 __device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, const ShiftTab &T, int code) {
-    const float4 sn = T.sn[code], sp = T.sp[code], lo = T.lo[code];
-    return make_float3(((xj.x + sn.x) - (xi.x - sp.x)) + lo.x, ((xj.y + sn.y) - (xi.y - sp.y)) + lo.y,
-                       ((xj.z + sn.z) - (xi.z - sp.z)) + lo.z);
+    const float4 sa = T.a[code], sb = T.b[code];
+    return make_float3(((xj.x + sa.x) - (xi.x - sb.x)) + sa.w, ((xj.y + sa.y) - (xi.y - sb.y)) + sb.w,
+                       (xj.z + sa.z) - (xi.z - sb.z));
 }
 
 // host-side launchers (defined in the kernel translation units)
