@@ -218,7 +218,10 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
 #endif
 constexpr int force_min_ctas(int tpa) { return RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1; }
 
-template <int POT, int TPA, bool M6, bool STG>
+// SAMPLE: this launch records a stress sample (slot >= 0) or evaluates the
+// energy and virial (MODE_EVAL); without it the pair loop skips the virial and
+// energy terms, which only feed those records.
+template <int POT, int TPA, bool M6, bool STG, bool SAMPLE>
 __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KParams p, KArrays a, int cur, int mode, int slot,
                                                        int step_index) {
     extern __shared__ __align__(16) float4 s_cell[];
@@ -269,14 +272,16 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
                     fx = fmaf(gr, dx, fx);
                     fy = fmaf(gr, dy, fy);
                     fz = fmaf(gr, dz, fz);
-                    const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
-                    w0 = fmaf(hx, dx, w0);
-                    w1 = fmaf(hy, dy, w1);
-                    w2 = fmaf(-0.5f * gr * dz, dz, w2);
-                    w3 = fmaf(hx, dy, w3);
-                    w4 = fmaf(hx, dz, w4);
-                    w5 = fmaf(hy, dz, w5);
-                    pe = fmaf(0.5f * eps, arn, pe);
+                    if (SAMPLE) {
+                        const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
+                        w0 = fmaf(hx, dx, w0);
+                        w1 = fmaf(hy, dy, w1);
+                        w2 = fmaf(-0.5f * gr * dz, dz, w2);
+                        w3 = fmaf(hx, dy, w3);
+                        w4 = fmaf(hx, dz, w4);
+                        w5 = fmaf(hy, dz, w5);
+                        pe = fmaf(0.5f * eps, arn, pe);
+                    }
                 }
             };
             if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
@@ -297,14 +302,16 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
                     fx = fmaf(gr, dx, fx);
                     fy = fmaf(gr, dy, fy);
                     fz = fmaf(gr, dz, fz);
-                    const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
-                    w0 = fmaf(hx, dx, w0);
-                    w1 = fmaf(hy, dy, w1);
-                    w2 = fmaf(-0.5f * gr * dz, dz, w2);
-                    w3 = fmaf(hx, dy, w3);
-                    w4 = fmaf(hx, dz, w4);
-                    w5 = fmaf(hy, dz, w5);
-                    pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
+                    if (SAMPLE) {
+                        const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
+                        w0 = fmaf(hx, dx, w0);
+                        w1 = fmaf(hy, dy, w1);
+                        w2 = fmaf(-0.5f * gr * dz, dz, w2);
+                        w3 = fmaf(hx, dy, w3);
+                        w4 = fmaf(hx, dz, w4);
+                        w5 = fmaf(hy, dz, w5);
+                        pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
+                    }
                 }
             };
             if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
@@ -314,13 +321,15 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     fx = sub_sum<TPA>(fx);
     fy = sub_sum<TPA>(fy);
     fz = sub_sum<TPA>(fz);
-    w0 = sub_sum<TPA>(w0);
-    w1 = sub_sum<TPA>(w1);
-    w2 = sub_sum<TPA>(w2);
-    w3 = sub_sum<TPA>(w3);
-    w4 = sub_sum<TPA>(w4);
-    w5 = sub_sum<TPA>(w5);
-    pe = sub_sum<TPA>(pe);
+    if (SAMPLE) {
+        w0 = sub_sum<TPA>(w0);
+        w1 = sub_sum<TPA>(w1);
+        w2 = sub_sum<TPA>(w2);
+        w3 = sub_sum<TPA>(w3);
+        w4 = sub_sum<TPA>(w4);
+        w5 = sub_sum<TPA>(w5);
+        pe = sub_sum<TPA>(pe);
+    }
     const bool own = live && sub == 0;
 
     if (own && POT == RC_POT_SC && xi.w > 0.0f) pe -= p.eps * p.sc_c / xi.w;  // embedding -eps c sqrt(rho_i)
@@ -444,15 +453,24 @@ void set_smem(K kernel, int bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+template <int POT, bool M6, bool STG, bool SAMPLE>
+void launch_force_tpa(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
+                      int step_index, int smem, cudaStream_t s) {
+    switch (tpa) {
+    case 1: k_force<POT, 1, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 2: k_force<POT, 2, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 4: k_force<POT, 4, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    default: k_force<POT, 8, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    }
+}
+
 template <int POT, bool M6, bool STG>
 void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
                       int step_index, int smem, cudaStream_t s) {
-    switch (tpa) {
-    case 1: k_force<POT, 1, M6, STG><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 2: k_force<POT, 2, M6, STG><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 4: k_force<POT, 4, M6, STG><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    default: k_force<POT, 8, M6, STG><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    }
+    if (slot >= 0 || mode == MODE_EVAL)
+        launch_force_tpa<POT, M6, STG, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
+    else
+        launch_force_tpa<POT, M6, STG, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
 }
 
 template <bool M6, bool STG>
@@ -465,12 +483,18 @@ void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, 
     }
 }
 
+template <int POT, bool M6, bool SAMPLE>
+void prepare_pot_s(int bytes) {
+    set_smem(k_force<POT, 1, M6, true, SAMPLE>, bytes);
+    set_smem(k_force<POT, 2, M6, true, SAMPLE>, bytes);
+    set_smem(k_force<POT, 4, M6, true, SAMPLE>, bytes);
+    set_smem(k_force<POT, 8, M6, true, SAMPLE>, bytes);
+}
+
 template <int POT, bool M6>
 void prepare_pot(int bytes) {
-    set_smem(k_force<POT, 1, M6, true>, bytes);
-    set_smem(k_force<POT, 2, M6, true>, bytes);
-    set_smem(k_force<POT, 4, M6, true>, bytes);
-    set_smem(k_force<POT, 8, M6, true>, bytes);
+    prepare_pot_s<POT, M6, true>(bytes);
+    prepare_pot_s<POT, M6, false>(bytes);
 }
 
 template <bool M6>

@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
         const int *bs = a.bin_start + a.bin_off[c];
         int4 pr = make_int4(-1, -1, -1, -1);
         if (p.pot == RC_POT_KG) pr = a.partner[g];
+        // two sweeps of the stencil: central-image neighbours first, then the
+        // periodic images, so that the lanes of a warp walk long runs of
+        // central entries, which skip the shift-table loads
+        for (int sweep = 0; sweep < 2; sweep++)
         for (int o0 = -1; o0 <= 1; o0++) {
             int u0 = b0 + o0, s0 = u0 < 0 ? -1 : (u0 >= nb0 ? 1 : 0);
             u0 -= s0 * nb0;
@@ -194,10 +198,11 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                     int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
                     u2 -= s2 * nb2;
                     const int code = (s0 + 1) + 3 * (s1 + 1) + 9 * (s2 + 1);
+                    if ((code == RC_CODE_CENTRAL) != (sweep == 0)) continue;
                     const int bb = (u0 * nb1 + u1) * nb2 + u2;
                     const int j0 = bs[bb], j1 = bs[bb + 1];
                     for (int jl = j0; jl < j1; jl++) {
-                        if (jl == li && code == 13) continue;
+                        if (jl == li && code == RC_CODE_CENTRAL) continue;
                         if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
                         const float4 xj = X[off + jl];
                         const float3 d = rc_disp(xi, xj, s_tab, code);
