@@ -131,10 +131,16 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
             if (gnn < ng) enn = __ldg(nb4 + (size_t)gnn * RC_TILE);
         }
         const int left = nn - 4 * g;
-        fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
-        if (left > 1) fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
-        if (left > 2) fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
-        if (left > 3) fn(c3, rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS));
+        if (left >= 4) {  // full group
+            fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
+            fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
+            fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
+            fn(c3, rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS));
+        } else {  // the list's last, partial group
+            fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
+            if (left > 1) fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
+            if (left > 2) fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
+        }
         if (gn >= ng) break;
         g = gn;
         gn = gnn;

@@ -145,16 +145,14 @@ __device__ __forceinline__ void rc_load_shifts(ShiftTab &T, float *s_H, const fl
     __syncthreads();
 }
 
-// The central image (code 13) needs no table entry: its shifts are zero and the
-// displacement reduces to x_j - x_i, bit for bit; only the other codes load.
+// The central image (code 13) has all-zero table entries, so its displacement is
+// x_j - x_i bit for bit.  Lists hold their central entries first: lanes of a
+// warp then mostly read the same (central) entry, which shared memory serves
+// as one broadcast.
 constexpr int RC_CODE_CENTRAL = 13;
 
 __device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, const ShiftTab &T, int code) {
-    float4 sa = make_float4(0.f, 0.f, 0.f, 0.f), sb = sa;
-    if (code != RC_CODE_CENTRAL) {
-        sa = T.a[code];
-        sb = T.b[code];
-    }
+    const float4 sa = T.a[code], sb = T.b[code];
     return make_float3(((xj.x + sa.x) - (xi.x - sb.x)) + sa.w, ((xj.y + sa.y) - (xi.y - sb.y)) + sb.w,
                        (xj.z + sa.z) - (xi.z - sb.z));
 }
