@@ -82,11 +82,11 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
  * `stream`. */
 int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream);
 
-/* GEMM engine for the forward and data-gradient products: 0 = warp-level BF16
- * tensor-core instructions (mma.sync, the default), 1 = 5th-generation tensor
- * cores (tcgen05: operands in shared memory, FP32 accumulator in tensor
- * memory).  Weight gradients always use the first.  Same results up to
- * summation order. */
+/* GEMM engine for the forward and data-gradient products: 1 = 5th-generation
+ * tensor cores (tcgen05: operands in shared memory, FP32 accumulator in tensor
+ * memory; the default), 0 = warp-level BF16 tensor-core instructions
+ * (mma.sync).  Weight gradients always use the second.  Same results up to
+ * summation order.  RC_EINVAL for another value. */
 int sur_set_backend(sur_ctx *s, int backend);
 
 /* Wait for the stream; return RC_ETIMEOUT if a bounded tensor-core wait gave up,

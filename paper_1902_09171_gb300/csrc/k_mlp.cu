@@ -1,7 +1,10 @@
 // Recurrent-MLP stress surrogate on tensor cores: BF16 operands, FP32
-// accumulation (mma.sync m16n8k16), fused epilogues, BPTT and AdamW.
+// accumulation, fused epilogues, BPTT and AdamW.  Two GEMM engines: tcgen05
+// (5th-generation tensor cores, accumulator in tensor memory; the default for
+// the forward and data-gradient products) and warp-level mma.sync m16n8k16
+// (weight gradients, which read A transposed, and the alternative engine).
 //
-// GEMM: C[M x N] = op(A)[M x K] * B[K x N], op(A) = A (row-major, lda) or A^T
+// mma.sync GEMM: C[M x N] = op(A)[M x K] * B[K x N], op(A) = A (row-major, lda) or A^T
 // (A stored K x M).  CTA tile 64 x 64 x 32, four warps of 32 x 32; operand
 // tiles staged in shared memory (A as [m][k], B as [n][k], k contiguous, so
 // every fragment register is one aligned 32-bit shared load).  Epilogues fuse
@@ -80,6 +83,46 @@ __device__ __forceinline__ void epilogue(const Epi &e, int m, int n, int M, int 
         e.s_out[(size_t)m * e.s_ld + n] = acc;
     } else {  // EPI_WGRAD: split-K partial sums
         atomicAdd(&e.s_out[(size_t)m * e.s_ld + n], acc);
+    }
+}
+
+// Sixteen consecutive columns n..n+15 of row m (n a multiple of 16, N a
+// multiple of 16) with 16-byte loads and stores; the head epilogue, whose
+// outputs are not 16-byte aligned, goes element by element.
+template <int EPI>
+__device__ __forceinline__ void epilogue16(const Epi &e, int m, int n, int M, int N, const float (&acc)[16]) {
+    if (m >= M || n >= N) return;
+    if (EPI == EPI_GELU) {
+        __align__(16) __nv_bfloat16 y[16], a[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const float v = acc[j] + e.bias[n + j];
+            y[j] = __float2bfloat16(v);
+            a[j] = __float2bfloat16(gelu_f(v));
+        }
+        uint4 *py = reinterpret_cast<uint4 *>(e.y_out + (size_t)m * e.ld_out + n);
+        uint4 *pa = reinterpret_cast<uint4 *>(e.a_out + (size_t)m * e.ld_out + n);
+        py[0] = reinterpret_cast<const uint4 *>(y)[0];
+        py[1] = reinterpret_cast<const uint4 *>(y)[1];
+        pa[0] = reinterpret_cast<const uint4 *>(a)[0];
+        pa[1] = reinterpret_cast<const uint4 *>(a)[1];
+    } else if (EPI == EPI_DGELU) {
+        __align__(16) __nv_bfloat16 y[16], d[16];
+        const uint4 *py = reinterpret_cast<const uint4 *>(e.y_in + (size_t)m * e.ld_in + n);
+        reinterpret_cast<uint4 *>(y)[0] = py[0];
+        reinterpret_cast<uint4 *>(y)[1] = py[1];
+#pragma unroll
+        for (int j = 0; j < 16; j++) d[j] = __float2bfloat16(acc[j] * gelu_d(__bfloat162float(y[j])));
+        uint4 *pd = reinterpret_cast<uint4 *>(e.a_out + (size_t)m * e.ld_out + n);
+        pd[0] = reinterpret_cast<const uint4 *>(d)[0];
+        pd[1] = reinterpret_cast<const uint4 *>(d)[1];
+    } else if (EPI == EPI_F32) {
+        float4 *p = reinterpret_cast<float4 *>(e.s_out + (size_t)m * e.s_ld + n);
+#pragma unroll
+        for (int j = 0; j < 4; j++) p[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) epilogue<EPI>(e, m, n + j, M, N, acc[j]);
     }
 }
 
@@ -182,14 +225,15 @@ void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *
 // The same GEMM on the 5th-generation tensor cores (tcgen05): C[M x N] =
 // A[M x K] * Bk[N x K]^T with both operands K-major.  One CTA computes a
 // 128 x 64 tile with the whole K (<= 256) resident in shared memory:
-//   * operands are written to shared memory in the K-major "core matrix"
-//     layout (8 rows x 16 bytes per core matrix, no swizzle): core (r/8, k/8)
-//     at byte (k/8 * rows/8 + r/8) * 128, row r%8 at +16 (r%8);
+//   * operands are copied (cp.async, 16 bytes per copy) into shared memory in
+//     the K-major "core matrix" layout (8 rows x 16 bytes per core matrix, no
+//     swizzle): core (r/8, k/8) at byte (k/8 * rows/8 + r/8) * 128, row r%8 at
+//     +16 (r%8);
 //   * one elected thread issues K/16 tcgen05.mma (kind::f16, BF16 inputs,
 //     FP32 accumulator in tensor memory) and a tcgen05.commit onto an mbarrier;
 //   * every warp waits on the mbarrier (bounded), reads its 32 accumulator rows
-//     with tcgen05.ld and runs the fused epilogue; tensor memory is freed on
-//     every path.
+//     with tcgen05.ld and runs the fused epilogue sixteen columns at a time
+//     with 16-byte stores; tensor memory is freed on every path.
 // ---------------------------------------------------------------------------
 constexpr int TC_M = 128, TC_N = 64, TC_THREADS = 128, TC_SPIN = 1 << 22;
 
@@ -220,20 +264,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *_
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // operands into the core-matrix layout
-    const uint4 z4 = make_uint4(0, 0, 0, 0);
+    // operands into the core-matrix layout with asynchronous 16-byte copies (all
+    // of a thread's copies in flight at once; rows past the matrix are zero-filled)
     for (int idx = tid; idx < TC_M * KC; idx += TC_THREADS) {
         const int r = idx / KC, kc = idx - r * KC;
-        uint4 v = z4;
-        if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + kc * 8);
-        *reinterpret_cast<uint4 *>(sA + ((size_t)kc * (TC_M / 8) + (r >> 3)) * 128 + (r & 7) * 16) = v;
+        const bool in = m0 + r < M;
+        const __nv_bfloat16 *src = A + (size_t)(in ? m0 + r : 0) * lda + kc * 8;
+        const unsigned dst =
+            (unsigned)__cvta_generic_to_shared(sA + ((size_t)kc * (TC_M / 8) + (r >> 3)) * 128 + (r & 7) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
     }
     for (int idx = tid; idx < TC_N * KC; idx += TC_THREADS) {
         const int r = idx / KC, kc = idx - r * KC;
-        uint4 v = z4;
-        if (n0 + r < N) v = *reinterpret_cast<const uint4 *>(Bk + (size_t)(n0 + r) * ldb + kc * 8);
-        *reinterpret_cast<uint4 *>(sB + ((size_t)kc * (TC_N / 8) + (r >> 3)) * 128 + (r & 7) * 16) = v;
+        const bool in = n0 + r < N;
+        const __nv_bfloat16 *src = Bk + (size_t)(in ? n0 + r : 0) * ldb + kc * 8;
+        const unsigned dst =
+            (unsigned)__cvta_generic_to_shared(sB + ((size_t)kc * (TC_N / 8) + (r >> 3)) * 128 + (r & 7) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
     if (tid == 0) {
@@ -287,8 +339,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *_
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; j++) epilogue<EPI>(e, row, n0 + c0 + j, M, N, __uint_as_float(r[j]));
+            for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+            epilogue16<EPI>(e, row, n0 + c0, M, N, v);
         }
     } else if (tid == 0) {
         atomicExch(err, RC_ETIMEOUT);
@@ -464,7 +518,7 @@ struct sur_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int K = 0, Bmax = 0, Tmax = 0;
-    int backend = 0;  // 0: mma.sync kernels, 1: tcgen05 kernels for the forward and data-gradient GEMMs
+    int backend = 1;  // 1: tcgen05 kernels for the forward and data-gradient GEMMs, 0: mma.sync kernels
     int *d_err = nullptr;
     std::vector<SurMember> mem;
     std::vector<void *> allocs;
