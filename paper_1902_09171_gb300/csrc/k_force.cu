@@ -217,10 +217,11 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
 }
 
 // Resident CTAs per SM the force kernel is compiled for at one lane per atom
-// (caps its registers at 65536 / (128 * RC_FORCE_MIN_CTAS)); 1 leaves the
+// (caps its registers at 65536 / (128 * RC_FORCE_MIN_CTAS)).  7 keeps a
+// 128 000-atom batch (1000 tiles) in one wave on 152 SMs; 1 leaves the
 // register count to the compiler.
 #ifndef RC_FORCE_MIN_CTAS
-#define RC_FORCE_MIN_CTAS 1
+#define RC_FORCE_MIN_CTAS 7
 #endif
 constexpr int force_min_ctas(int tpa) { return RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1; }
 
