@@ -82,11 +82,13 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
  * `stream`. */
 int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream);
 
-/* GEMM engine for the forward and data-gradient products: 1 = 5th-generation
- * tensor cores (tcgen05: operands in shared memory, FP32 accumulator in tensor
- * memory; the default), 0 = warp-level BF16 tensor-core instructions
- * (mma.sync).  Weight gradients always use the second.  Same results up to
- * summation order.  RC_EINVAL for another value. */
+/* Tensor-core engine: 2 = the whole recurrent forward (all layers, all steps)
+ * in one 5th-generation tensor-core (tcgen05) kernel per 128-row tile, with
+ * the activations on chip, and one tcgen05 GEMM per layer and step for the
+ * data gradients (the default); 1 = one tcgen05 GEMM per layer and step for
+ * both; 0 = warp-level BF16 instructions (mma.sync) for both.  Weight
+ * gradients always use mma.sync.  Same results up to summation order.
+ * RC_EINVAL for another value. */
 int sur_set_backend(sur_ctx *s, int backend);
 
 /* Wait for the stream; return RC_ETIMEOUT if a bounded tensor-core wait gave up,

@@ -380,6 +380,285 @@ void prepare_tc05() {
 }
 
 // ---------------------------------------------------------------------------
+// The whole recurrent forward in one kernel (tcgen05).  A CTA owns 128 rows of
+// the batch (one member: blockIdx.y) and walks all T steps: per step the four
+// layers run back to back on the tensor cores, with the activations kept in
+// shared memory (BF16, K-major core-matrix layout) and the layer accumulator
+// (128 x 256 FP32) in tensor memory.  Weights (Wt, N x K) stream through four
+// shared buffers of 64 rows each: copies run three chunks ahead of the MMAs,
+// and a buffer is refilled once the MMAs that read it have completed (one
+// mbarrier per buffer, bounded waits).  Epilogues run in
+// 16 warps (warp w: accumulator rows 32 (w % 4).., column quarter w / 4): bias +
+// GELU into the next layer's operand; the head writes the stress and the new
+// state h = tanh(.) straight into the next step's input rows.  With a tape
+// (training) every step's z, y and a rows also go to global memory for the
+// backward pass, in the layout the layer-wise kernels use.
+// ---------------------------------------------------------------------------
+constexpr int FT_THREADS = 512, FT_PARTS = FT_THREADS / 128, FT_M = 128, FT_NC = 64, FT_MAXK = 8;
+// The input rows z (128 x 144) and the activations (128 x 256) share one
+// buffer: z is dead once layer 1's MMAs have read it, and the head writes the
+// next step's state after the last layer's MMAs have read the activations.
+constexpr int FT_NBUF = 4;  // weight buffers: copies run up to three chunks ahead of the MMAs
+constexpr int FT_SA = FT_M * WID * 2, FT_SW = FT_NC * WID * 2;
+constexpr int FT_SMEM = FT_SA + FT_NBUF * FT_SW;
+static_assert(FT_NBUF >= 2 && FT_NBUF <= 4, "cp_async_wait_upto covers up to two pending groups");
+constexpr int FT_CHUNKS = 4 + 4 + 4 + 3;  // weight chunks of 64 rows per step (N = 256, 256, 256, 144)
+
+struct FusedArgs {
+    const float *U;      // (B, T, NIN) raw features (row b, step t at (b * T + t) * NIN)
+    int B, T;
+    const float *u_inv;  // NIN feature scales
+    const float *s_mul;  // NOUT output scales, or null (network units)
+    float *S;            // stress: member k, row b, step t at S + k * s_mstride + b * s_ld + t * NOUT
+    long s_mstride;
+    int s_ld;
+    float *h;            // FP32 state (member k, row b at h + k * h_mstride + b * NH): read at step 0 and
+    long h_mstride;      // overwritten with the final state; null: zero initial state, not written
+    __nv_bfloat16 *tZ, *tY[3], *tA[3];  // tape (member 0 only), or null
+    const __nv_bfloat16 *Wt[FT_MAXK][4];
+    const float *theta[FT_MAXK];
+    int *err;
+};
+
+// byte offset of element (r, k) in a K-major core-matrix tile with `rows` rows
+__device__ __forceinline__ unsigned cm_off(int r, int k, int rows) {
+    return (unsigned)((((k >> 3) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ unsigned mbar_try(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done;
+}
+
+// every thread waits (bounded) for the phase with the given parity; the block
+// agrees on the outcome
+__device__ __forceinline__ bool mbar_wait_all(unsigned bar, unsigned parity) {
+    unsigned done = 0;
+    for (int it = 0; it < TC_SPIN && !done; it++) done = mbar_try(bar, parity);
+    return __syncthreads_and(done) != 0;
+}
+
+// copy weight chunk q (rows 64 q .. 64 q + 63 of the N x K matrix Wt, zero past N)
+// into a 64-row core-matrix buffer: all threads, one cp.async group
+__device__ __forceinline__ void ft_load_chunk(unsigned char *dst, const __nv_bfloat16 *Wt, int N, int K, int q) {
+    const int KC = K >> 3;
+    for (int idx = threadIdx.x; idx < FT_NC * KC; idx += FT_THREADS) {
+        const int r = idx / KC, kc = idx - r * KC, n = q * FT_NC + r;
+        const bool in = n < N;
+        const __nv_bfloat16 *src = Wt + (size_t)(in ? n : 0) * K + kc * 8;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + cm_off(r, kc * 8, FT_NC));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// chunk c of the per-step weight sequence (layers 1..4, 64-row chunks) into buffer c % FT_NBUF
+__device__ __forceinline__ void ft_load_chunk_seq(unsigned char *sW, const __nv_bfloat16 *const *Wt, long c) {
+    const int j = (int)(c % FT_CHUNKS);
+    const int l = j < 4 ? 0 : (j < 8 ? 1 : (j < 12 ? 2 : 3)), q = j - 4 * l;
+    ft_load_chunk(sW + (c % FT_NBUF) * FT_SW, Wt[l], l == 3 ? N4 : WID, l == 0 ? K0 : WID, q);
+}
+
+// wait until at most n of this thread's copy groups are pending (0 <= n <= FT_NBUF - 2)
+__device__ __forceinline__ void cp_async_wait_upto(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float v) {
+    const __nv_bfloat16 b = __float2bfloat16(v);
+    return *reinterpret_cast<const unsigned short *>(&b);
+}
+
+__global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
+    extern __shared__ __align__(1024) unsigned char ft_smem[];
+    __shared__ __align__(8) unsigned long long s_bar[FT_NBUF];
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
+    unsigned char *sZ = ft_smem, *sA = ft_smem, *sW = ft_smem + FT_SA;
+    const float *theta = a.theta[mk];
+    float *S = a.S + mk * a.s_mstride;
+    float *h = a.h ? a.h + mk * a.h_mstride : nullptr;
+    const bool tape = a.tZ != nullptr;
+    const int B = a.B, T = a.T;
+
+    if (warp == 0) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(WID)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
+    if (tid == 0) {
+        for (int i = 0; i < FT_NBUF; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * i) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const long n_chunks = (long)T * FT_CHUNKS;
+    for (long c0 = 0; c0 < FT_NBUF - 1 && c0 < n_chunks; c0++) ft_load_chunk_seq(sW, a.Wt[mk], c0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    long c = 0;  // chunks whose MMAs have been issued
+    bool ok = true;
+    const int quarter = warp & 3, part = warp >> 2, row = quarter * 32 + lane, b = m0 + row;
+
+    for (int t = 0; t < T && ok; t++) {
+        // (a) input rows z_t = [u_t * u_inv, h (written by the head of step t-1; given or zero at
+        //     step 0), 0]
+        for (int idx = tid; idx < FT_M * 16; idx += FT_THREADS) {
+            const int r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1, bb = m0 + r;
+            const float v = (j < NIN && bb < B) ? a.U[((size_t)bb * T + t) * NIN + j] * a.u_inv[j] : 0.0f;
+            const unsigned short hv = bf16_bits(v);
+            *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = hv;
+            if (tape && bb < B) reinterpret_cast<unsigned short *>(a.tZ)[((size_t)t * B + bb) * K0 + col] = hv;
+        }
+        if (t == 0) {
+            for (int idx = tid; idx < FT_M * NH; idx += FT_THREADS) {
+                const int r = idx / NH, j = idx - r * NH, bb = m0 + r;
+                const float v = (h && bb < B) ? h[(size_t)bb * NH + j] : 0.0f;
+                const unsigned short hv = bf16_bits(v);
+                *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = hv;
+                if (tape && bb < B) reinterpret_cast<unsigned short *>(a.tZ)[(size_t)bb * K0 + NIN + j] = hv;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // (b) the four layers
+        for (int l = 0; l < 4 && ok; l++) {
+            const int Kl = l == 0 ? K0 : WID, Nl = l == 3 ? N4 : WID, nq = l == 3 ? 3 : 4;
+            const unsigned aBase = (unsigned)__cvta_generic_to_shared(l == 0 ? sZ : sA);
+            for (int q = 0; q < nq && ok; q++, c++) {
+                // chunk c has landed (this thread's copies), and every thread's copies are visible
+                // to the tensor cores
+                cp_async_wait_upto((int)((c + FT_NBUF - 2 < n_chunks - 1 ? c + FT_NBUF - 2 : n_chunks - 1) - c));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int buf = (int)(c % FT_NBUF);
+                if (tid == 0) {
+                    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
+                                           ((unsigned)(FT_M >> 4) << 24);
+                    const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + buf * FT_SW);
+                    const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
+                    const unsigned dcol = tmem + (unsigned)(q * FT_NC);
+                    for (int kk = 0; kk < (Kl >> 4); kk++) {
+                        const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
+                        const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
+                        const unsigned acc = kk > 0;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     bar0 + 8 * buf)
+                                 : "memory");
+                }
+                // refill the buffer of chunk c - 1 with chunk c + FT_NBUF - 1 once chunk c - 1's MMAs
+                // (its last reader) are done
+                if (c + FT_NBUF - 1 < n_chunks) {
+                    if (c >= 1) ok = mbar_wait_all(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
+                    if (ok) ft_load_chunk_seq(sW, a.Wt[mk], c + FT_NBUF - 1);
+                }
+            }
+            if (!ok) break;
+            // the layer's accumulator is complete once the MMAs of its last chunk are
+            ok = mbar_wait_all(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // (c) epilogue: this warp's 32 rows, its quarter of the columns, 16 at a time
+            const int nch = Nl >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
+            for (int ch = ch0; ch < ch1; ch++) {
+                const int n0 = ch * 16;
+                unsigned r[16];
+                const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (l < 3) {
+                    const float *bias = theta + (l == 0 ? OFF_B1 : (l == 1 ? OFF_B2 : OFF_B3));
+                    unsigned yp[8], ap[8];  // BF16 pairs, low half = even column
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const float v0 = __uint_as_float(r[j]) + bias[n0 + j];
+                        const float v1 = __uint_as_float(r[j + 1]) + bias[n0 + j + 1];
+                        yp[j >> 1] = (unsigned)bf16_bits(v0) | ((unsigned)bf16_bits(v1) << 16);
+                        ap[j >> 1] = (unsigned)bf16_bits(gelu_f(v0)) | ((unsigned)bf16_bits(gelu_f(v1)) << 16);
+                    }
+                    const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
+                    *reinterpret_cast<uint4 *>(sA + cm_off(row, n0, FT_M)) = a0;
+                    *reinterpret_cast<uint4 *>(sA + cm_off(row, n0 + 8, FT_M)) = a1;
+                    if (tape && b < B) {
+                        uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + ((size_t)t * B + b) * WID + n0);
+                        uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + ((size_t)t * B + b) * WID + n0);
+                        py[0] = make_uint4(yp[0], yp[1], yp[2], yp[3]);
+                        py[1] = make_uint4(yp[4], yp[5], yp[6], yp[7]);
+                        pa[0] = a0;
+                        pa[1] = a1;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int n = n0 + j;
+                        const float o = __uint_as_float(r[j]) + theta[OFF_B4 + n];
+                        if (n < NOUT) {
+                            if (b < B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
+                        } else if (n < NOUT + NH) {
+                            const float hv = tanhf(o);
+                            const unsigned short hb = bf16_bits(hv);
+                            *reinterpret_cast<unsigned short *>(sZ + cm_off(row, NIN + n - NOUT, FT_M)) = hb;
+                            if (tape && b < B && t + 1 < T)
+                                reinterpret_cast<unsigned short *>(a.tZ)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] =
+                                    hb;
+                            if (h && b < B && t + 1 == T) h[(size_t)b * NH + n - NOUT] = hv;
+                        }
+                    }
+                }
+            }
+            // the activations written above are read by the next MMAs (async proxy), and the
+            // accumulator is overwritten by them
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(a.err, RC_ETIMEOUT);
+        // let the tensor-core work and copies in flight finish before their memory is released
+        if (c >= 1) {
+            unsigned done = 0;
+            for (int it = 0; it < TC_SPIN && !done; it++)
+                done = mbar_try(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WID) : "memory");
+    }
+}
+
+void prepare_fused() {
+    cudaFuncSetAttribute(k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
+}
+
+// ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
 
@@ -518,7 +797,9 @@ struct sur_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int K = 0, Bmax = 0, Tmax = 0;
-    int backend = 1;  // 1: tcgen05 kernels for the forward and data-gradient GEMMs, 0: mma.sync kernels
+    // 2: whole-forward tcgen05 kernel + tcgen05 data-gradient GEMMs (the default), 1: tcgen05 GEMM
+    // per layer and step, 0: mma.sync GEMMs
+    int backend = 2;
     int *d_err = nullptr;
     std::vector<SurMember> mem;
     std::vector<void *> allocs;
@@ -552,7 +833,47 @@ void cast_member(sur_ctx *s, SurMember &M) {
 }
 
 // forward through T steps for member M; stress predictions into S (B x T x 6)
+// Whole-forward kernel for members k0 .. k0 + nk - 1 (see k_forward_fused).
+void forward_fused(sur_ctx *s, int k0, int nk, const float *U, int B, int T, float *S, long s_mstride, int s_ld,
+                   const float *s_mul, float *h, long h_mstride, bool tape) {
+    for (int g = 0; g < nk; g += FT_MAXK) {
+        const int ng = std::min(FT_MAXK, nk - g);
+        FusedArgs a{};
+        a.U = U;
+        a.B = B;
+        a.T = T;
+        a.u_inv = s->u_inv;
+        a.s_mul = s_mul;
+        a.S = S + (size_t)g * s_mstride;
+        a.s_mstride = s_mstride;
+        a.s_ld = s_ld;
+        a.h = h ? h + (size_t)g * h_mstride : nullptr;
+        a.h_mstride = h_mstride;
+        if (tape) {
+            a.tZ = s->Z;
+            a.tY[0] = s->Y1;
+            a.tY[1] = s->Y2;
+            a.tY[2] = s->Y3;
+            a.tA[0] = s->A1;
+            a.tA[1] = s->A2;
+            a.tA[2] = s->A3;
+        }
+        for (int i = 0; i < ng; i++) {
+            for (int l = 0; l < 4; l++) a.Wt[i][l] = s->mem[k0 + g + i].Wt[l];
+            a.theta[i] = s->mem[k0 + g + i].theta;
+        }
+        a.err = s->d_err;
+        dim3 grid(cdiv(B, FT_M), ng);
+        k_forward_fused<<<grid, FT_THREADS, FT_SMEM, s->stream>>>(a);
+    }
+}
+
 void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, const float *s_mul) {
+    if (s->backend == 2) {
+        const int k = (int)(&M - s->mem.data());
+        forward_fused(s, k, 1, U, B, T, S, 0, T * NOUT, s_mul, nullptr, 0, true);
+        return;
+    }
     const size_t RB = (size_t)B;
     for (int t = 0; t < T; t++) {
         __nv_bfloat16 *Zt = s->Z + (size_t)t * RB * K0;
@@ -693,6 +1014,7 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
     ok &= salloc(s, &s->loss_acc, 1) == cudaSuccess;
     ok &= salloc(s, &s->d_err, 1) == cudaSuccess;
     prepare_tc05();
+    prepare_fused();
     s->mem.resize(n_members);
     for (auto &M : s->mem) {
         ok &= salloc(s, &M.theta, NPAR) == cudaSuccess;
@@ -801,12 +1123,21 @@ int sur_train_step(sur_ctx *s, const float *U, const float *Y, int B, int T, flo
 int sur_predict(sur_ctx *s, const float *U, int B, int T, float *Sout) {
     if (!s || !U || !Sout) return RC_EINVAL;
     if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
+    if (s->backend == 2) {
+        forward_fused(s, 0, s->K, U, B, T, Sout, (long)B * T * NOUT, T * NOUT, s->s_mul, nullptr, 0, false);
+        return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+    }
     for (int k = 0; k < s->K; k++) forward(s, s->mem[k], U, B, T, Sout + (size_t)k * B * T * NOUT, s->s_mul);
     return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
 }
 
 int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *s_mean, float *spread) {
     if (!s || !u || !h || !s_mean || !spread || n <= 0 || n > s->Bmax) return RC_EINVAL;
+    if (s->backend == 2) {
+        forward_fused(s, 0, s->K, u, n, 1, s->Sm, (long)n * NOUT, NOUT, s->s_mul, h, (long)n * NH, false);
+        k_ensemble<<<cdiv(n, 128), 128, 0, s->stream>>>(s->Sm, s->K, n, s_floor, s_mean, spread);
+        return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+    }
     __nv_bfloat16 *Z = s->Z;  // n rows of [u, h, 0]
     __nv_bfloat16 *Ys[3] = {s->Y1, s->Y2, s->Y3}, *As_[3] = {s->A1, s->A2, s->A3};
     for (int k = 0; k < s->K; k++) {
@@ -842,7 +1173,7 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
 }
 
 int sur_set_backend(sur_ctx *s, int backend) {
-    if (!s || backend < 0 || backend > 1) return RC_EINVAL;
+    if (!s || backend < 0 || backend > 2) return RC_EINVAL;
     s->backend = backend;
     return RC_OK;
 }
