@@ -476,10 +476,30 @@ __device__ __forceinline__ unsigned short bf16_bits(float v) {
     return *reinterpret_cast<const unsigned short *>(&b);
 }
 
+// two floats to a BF16 pair (round to nearest even), low half = first
+__device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&p);
+}
+
+// GELU x/2 (1 + erf(x / sqrt 2)) with erf from the rational approximation of
+// Abramowitz & Stegun, Handbook of Mathematical Functions (1964), formula
+// 7.1.26 (|error| <= 1.5e-7 for x >= 0; odd extension), far below the BF16
+// rounding of the stored activations.
+__device__ __forceinline__ float gelu_as(float x) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float erf_abs = 1.0f - poly * __expf(-z * z);
+    return 0.5f * x * (1.0f + copysignf(erf_abs, x));
+}
+
 __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
     extern __shared__ __align__(1024) unsigned char ft_smem[];
     __shared__ __align__(8) unsigned long long s_bar[FT_NBUF];
     __shared__ unsigned s_tmem;
+    __shared__ __align__(16) float s_bias[3 * WID + N4];  // b1, b2, b3, b4
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
     unsigned char *sZ = ft_smem, *sA = ft_smem, *sW = ft_smem + FT_SA;
@@ -495,6 +515,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    for (int i = tid; i < 3 * WID + N4; i += FT_THREADS)
+        s_bias[i] = theta[i < WID ? OFF_B1 + i : (i < 2 * WID ? OFF_B2 + i - WID : (i < 3 * WID ? OFF_B3 + i - 2 * WID : OFF_B4 + i - 3 * WID))];
     const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
     if (tid == 0) {
         for (int i = 0; i < FT_NBUF; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * i) : "memory");
@@ -591,14 +613,17 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
                     : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (l < 3) {
-                    const float *bias = theta + (l == 0 ? OFF_B1 : (l == 1 ? OFF_B2 : OFF_B3));
+                    const float4 *bias = reinterpret_cast<const float4 *>(s_bias + l * WID + n0);
                     unsigned yp[8], ap[8];  // BF16 pairs, low half = even column
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        const float v0 = __uint_as_float(r[j]) + bias[n0 + j];
-                        const float v1 = __uint_as_float(r[j + 1]) + bias[n0 + j + 1];
-                        yp[j >> 1] = (unsigned)bf16_bits(v0) | ((unsigned)bf16_bits(v1) << 16);
-                        ap[j >> 1] = (unsigned)bf16_bits(gelu_f(v0)) | ((unsigned)bf16_bits(gelu_f(v1)) << 16);
+                    for (int j = 0; j < 16; j += 4) {
+                        const float4 bv = bias[j >> 2];
+                        const float v0 = __uint_as_float(r[j]) + bv.x, v1 = __uint_as_float(r[j + 1]) + bv.y;
+                        const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
+                        yp[j >> 1] = bf16x2_bits(v0, v1);
+                        yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
+                        ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
+                        ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
                     }
                     const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
                     *reinterpret_cast<uint4 *>(sA + cm_off(row, n0, FT_M)) = a0;
@@ -615,7 +640,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         const int n = n0 + j;
-                        const float o = __uint_as_float(r[j]) + theta[OFF_B4 + n];
+                        const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
                         if (n < NOUT) {
                             if (b < B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
                         } else if (n < NOUT + NH) {
