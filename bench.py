@@ -65,6 +65,25 @@ def mesh():
     return X, conn, mask, val
 
 
+# FE of the copper bar in units consistent with the r-cell stress: P in GPa,
+# lengths in A, time in ps, so that P * area (GPa A^2) = mass * acceleration
+# needs masses in units of 1e-25 kg = 60.2214 amu.  E_CU is the modulus used to
+# size the explicit step (0.5 h / c, c = sqrt(E / rho0)), the mass-proportional
+# damping (critical for the bar's fundamental mode) and the hourglass stiffness
+# (0.05 E).
+AMU_PER_FE_MASS = 60.2214
+E_CU = 130.0  # GPa
+
+
+def fe_params():
+    rho0 = 4 * MASS / A_LAT ** 3 / AMU_PER_FE_MASS
+    c = np.sqrt(E_CU / rho0)  # A / ps
+    h = NC * A_LAT
+    dt = 0.5 * h / c
+    damping = np.pi * c / (MESH[0] * h)  # 2 omega_1 of a bar fixed at one end
+    return rho0, dt, damping, 0.05 * E_CU
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -131,7 +150,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fp32_peak_tflops():
+def fp32_unit_peak_tflops():
     """FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128
     FP32 lanes x 2 FLOP per FMA x 2070 MHz."""
     return 152 * 128 * 2 * 2.070e9 / 1e12
@@ -139,12 +158,14 @@ def fp32_peak_tflops():
 
 def sc_algorithmic_flops_per_atom_step(rho):
     """Algorithmic FP32 work of one Sutton-Chen atom-step, counted once per
-    unordered pair inside rc (FMA = 2 FLOP): density pass 14 FLOP/pair, force
-    pass 44 FLOP/pair (see the design doc for the breakdown), plus 40 for the
-    integrator.  Returns (density_per_atom, force_per_atom, total_per_atom)."""
+    unordered pair inside rc (FMA = 2 FLOP): density pass 14 FLOP/pair (r^2,
+    (a/r)^m through r^-6); force pass 30 FLOP/pair for the (a/r)^9, (a/r)^6
+    combination and the force scalar, 12 for the f_i / f_j accumulation and 12
+    for the six virial components on the steps that record a stress sample;
+    40 FLOP/atom for the integrator and the Langevin force.  Returns
+    (density_per_atom, force_per_atom without sample, force_per_atom with sample)."""
     half_pairs = rho * 4.0 / 3.0 * np.pi * SC["rc"] ** 3 / 2.0
-    dens, force = 14.0 * half_pairs, 44.0 * half_pairs + 40.0
-    return dens, force, dens + force
+    return 14.0 * half_pairs, 42.0 * half_pairs + 40.0, 54.0 * half_pairs + 40.0
 
 
 def run_ours(args):
@@ -169,9 +190,8 @@ def run_ours(args):
     ctx = rcell.rcell_create(prm, cells, stream=stream)
     if args.tpa:
         rcell.rcell_set_tuning(ctx, args.tpa, -1)
-    # FE: rho0 of copper in amu/A^3 (4 atoms per a^3), dt / damping in ps
-    rho0 = 4 * MASS / A_LAT ** 3
-    fe = rcell.fe_create(X, conn, mask, val, rho0, 0.05, 1.0, 0.0, stream=stream)
+    rho0, dt_fe, damp_fe, hg_fe = fe_params()
+    fe = rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=stream)
     n_atoms = sum(len(c["x0"]) for c in cells)
     md = args.md_steps
     navg = min(N_AVG, md // 2)
@@ -186,6 +206,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if rcell.rcell_sync(ctx) != 0:
         raise RuntimeError("warm-up failed: " + rcell.rcell_last_error(ctx))
+    fp32_peak = rcell.rcell_fp32_peak(stream)  # roofline denominator, measured with warm clocks
     if world > 1:
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -234,14 +255,17 @@ def run_ours(args):
     # ---- per-kernel durations (CUDA events around each launch, same stream) ----
     prof = rcell_kernel_profile(ctx, stream, n_steps=args.profile_steps)
     rho = NC ** 3 * 4 / (NC * A_LAT) ** 3
-    dens_f, force_f, _ = sc_algorithmic_flops_per_atom_step(rho)
-    force_ms = prof["force"]
-    achieved = force_f * n_atoms / (force_ms / 1e3) / 1e12
-    peak = fp32_peak_tflops()
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_force<SC> (force + Verlet/Langevin + virial)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts and max clock)"}
+    _, force_ns, force_s = sc_algorithmic_flops_per_atom_step(rho)
+    # one load increment: md - navg force launches without a stress sample, navg with one
+    n_ns, n_s = md - navg, navg
+    t_ns, t_s = prof["force"], prof.get("force_sample", prof["force"])
+    achieved = (n_ns * force_ns + n_s * force_s) * n_atoms / ((n_ns * t_ns + n_s * t_s) / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "kernel": "k_force<SC> (force + Verlet/Langevin (+ virial on sampling steps))",
+                "peak_source": "measured: FFMA probe on this GPU (rcell_fp32_peak), %.2f TFLOP/s; unit-count "
+                               "figure 152 SMs x 128 lanes x 2 FLOP x 2070 MHz = %.2f TFLOP/s"
+                               % (fp32_peak, fp32_unit_peak_tflops())}
 
     rcell.fe_destroy(fe)
     rcell.rcell_destroy(ctx)

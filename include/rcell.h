@@ -195,17 +195,33 @@ int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
  * read-only cache.  Both give the same results up to summation order. */
 int rcell_set_staging(rcell_ctx *ctx, int staged);
 
+/* Neighbour-list builds per cell since creation (the initial build, one after
+ * every deformation, and those the skin test triggered): counts receives
+ * n_cells host values.  Synchronous.  RC_EINVAL for NULL arguments. */
+int rcell_get_rebuilds(rcell_ctx *ctx, unsigned long long *counts);
+
 /* Number of cells, total atoms, and the number of kernels the last rcell_run
  * enqueued (for launch accounting); any pointer may be NULL. */
 int rcell_info(const rcell_ctx *ctx, int *n_cells, long *n_atoms, long *launches_last_run);
 
+/* Measurement helper with no counterpart in the paper: the FP32 fused
+ * multiply-add throughput (TFLOP/s, FMA = 2 FLOP) this GPU sustains, from a
+ * kernel of independent FMA chains filling every SM (about 5 ms), timed with
+ * CUDA events on `stream` (NULL: the default stream).  *tflops receives the
+ * result (0 on error).  Synchronous.  RC_EINVAL for a NULL tflops, RC_ECUDA
+ * if a launch or an event fails. */
+int rcell_fp32_peak(void *stream, double *tflops);
+
 /* Measurement helper: run n_steps more MD steps (plus a re-application of the
  * current F and a stress reduction) launching kernels one by one, with CUDA
  * events on the context's stream around every launch; ms_out (8 host doubles)
- * receives the mean duration in ms of one launch of: neighbour sort, list
- * build, Sutton-Chen density pass, force/integrate kernel (steady-state steps),
- * deformation (QR/box), remap, stress reduction, other (0 when not launched).
- * Advances the MD state like rcell_run.  Synchronous. */
+ * receives the mean duration in ms of one launch of: [0] neighbour sort, [1]
+ * list build, [2] Sutton-Chen density pass, [3] force/integrate kernel on a
+ * steady-state step that records no stress sample, [4] deformation (QR/box),
+ * [5] remap, [6] stress reduction, [7] force/integrate kernel on a step that
+ * records a sample (0 when not launched).  The steps are those of
+ * rcell_run(n_steps, n_steps / 2): the MD state advances and the stress series
+ * holds the samples of this run afterwards.  Synchronous. */
 int rcell_profile_kernels(rcell_ctx *ctx, int n_steps, double *ms_out);
 
 /* Per-cell checkpoint (the state the MD engine keeps between FE steps, Sec. 2.1:

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     if (threadIdx.x == 0) {
         int go = a.need_rebuild[c] && a.status[c] == 0 && a.active[c];
         a.built[c] = go;
-        if (go) a.need_rebuild[c] = 0;
+        if (go) {
+            a.need_rebuild[c] = 0;
+            a.rebuilds[c]++;
+        }
         s_go = go;
     }
     __syncthreads();

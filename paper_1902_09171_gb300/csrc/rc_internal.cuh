@@ -59,6 +59,7 @@ struct KArrays {
     int *bin_start;      // bin_off[c] .. + nbins+1
     int *status;
     int *need_rebuild, *built;
+    unsigned long long *rebuilds;  // per cell: neighbour-list builds so far
     const int *active;   // per cell: 0 = skipped by every MD kernel (state frozen)
     const unsigned long long *evals;
     double *series;      // [cell][slot][RC_SAMPLE_W]

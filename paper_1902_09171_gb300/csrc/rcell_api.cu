@@ -280,6 +280,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     CKC(c, dalloc(L, &A.status, n_cells));
     CKC(c, dalloc(L, &A.need_rebuild, n_cells));
     CKC(c, dalloc(L, &A.built, n_cells));
+    CKC(c, dalloc(L, &A.rebuilds, n_cells));
     int *d_active = nullptr;
     CKC(c, dalloc(L, &d_active, n_cells));
     {
@@ -604,6 +605,13 @@ int rcell_set_tuning(rcell_ctx *c, int threads_per_atom, int use_graphs) {
     return RC_OK;
 }
 
+int rcell_get_rebuilds(rcell_ctx *c, unsigned long long *counts) {
+    if (!c || !counts) return RC_EINVAL;
+    CKC(c, cudaStreamSynchronize(c->stream));
+    CKC(c, cudaMemcpy(counts, c->ka.rebuilds, sizeof(unsigned long long) * c->n_cells, cudaMemcpyDeviceToHost));
+    return RC_OK;
+}
+
 int rcell_info(const rcell_ctx *c, int *n_cells, long *n_atoms, long *launches_last_run) {
     if (!c) return RC_EINVAL;
     if (n_cells) *n_cells = c->n_cells;
@@ -705,8 +713,13 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
     CKC(c, cudaEventSynchronize(ev[2]));
     lap(0, 1, 4);
     lap(1, 2, 5);
+    // the steps of a run of n_steps that samples its last half, as rcell_run(n_steps, n_steps / 2)
+    const int n_avg = std::min(n_steps / 2, c->series_cap);
+    CKC(c, cudaMemsetAsync(c->ka.series, 0, sizeof(double) * (size_t)c->n_cells * c->series_cap * RC_SAMPLE_W,
+                           c->stream));
     for (int s = 0; s <= n_steps; s++) {
         const int mode = s == 0 ? MODE_SETUP : (s == n_steps ? MODE_LAST : MODE_STEP);
+        const int slot = (s > 0 && s > n_steps - n_avg) ? s - (n_steps - n_avg) - 1 : -1;
         CKC(c, cudaEventRecord(ev[0], c->stream));
         rc_launch_sort(c->kp, c->ka, c->cur, c->n_cells, c->stream);
         CKC(c, cudaEventRecord(ev[1], c->stream));
@@ -714,16 +727,17 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
         CKC(c, cudaEventRecord(ev[2], c->stream));
         if (c->kp.pot == RC_POT_SC) rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, stage_atoms(c), c->stream);
         CKC(c, cudaEventRecord(ev[3], c->stream));
-        rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, -1, s, stage_atoms(c), c->stream);
+        rc_launch_force(c->kp, c->ka, c->cur, c->n_tiles, c->tpa, mode, slot, s, stage_atoms(c), c->stream);
         CKC(c, cudaEventRecord(ev[4], c->stream));
         CKC(c, cudaEventSynchronize(ev[4]));
         lap(0, 1, 0);
         lap(1, 2, 1);
         if (c->kp.pot == RC_POT_SC) lap(2, 3, 2);
-        if (s > 0) lap(3, 4, 3);  // steady-state force launches only
+        if (s > 0) lap(3, 4, slot >= 0 ? 7 : 3);  // steady-state force launches only
         if (mode != MODE_LAST) c->cur ^= 1;
     }
     rc_launch_advance(c->d_evals, c->ka.active, c->n_cells, n_steps + 1, c->stream);
+    c->last_n_avg = n_avg;
     if (c->last_n_avg > 0) {
         CKC(c, cudaEventRecord(ev[0], c->stream));
         rc_launch_stress(c->ka.series, c->last_n_avg, c->series_cap, c->d_H, c->d_Q, c->d_F, pconv_of(c->prm.units),

@@ -47,7 +47,7 @@ class rcell_init(C.Structure):
 _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
-           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_info", "rcell_profile_kernels", "rcell_checkpoint", "rcell_restore",
+           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
            "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
@@ -80,6 +80,8 @@ def load(path: str | None = None):
         "rcell_set_tuning": ([vp, C.c_int, C.c_int], C.c_int),
         "rcell_info": ([vp, I, C.POINTER(C.c_long), C.POINTER(C.c_long)], C.c_int),
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
+        "rcell_fp32_peak": ([vp, vp], C.c_int),
+        "rcell_get_rebuilds": ([vp, vp], C.c_int),
         "rcell_checkpoint": ([vp, C.c_int, vp, C.POINTER(C.c_size_t)], C.c_int),
         "rcell_restore": ([vp, C.c_int, vp, C.c_size_t], C.c_int),
         "rcell_stress_reduce_static": ([vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -266,7 +268,7 @@ def rcell_info(ctx):
     return n.value, na.value, kl.value
 
 
-PROFILE_NAMES = ["sort", "nlist", "density", "force", "deform", "remap", "stress", "other"]
+PROFILE_NAMES = ["sort", "nlist", "density", "force", "deform", "remap", "stress", "force_sample"]
 
 
 def rcell_profile_kernels(ctx, n_steps: int):
@@ -274,6 +276,23 @@ def rcell_profile_kernels(ctx, n_steps: int):
     out = np.zeros(8)
     _check(load().rcell_profile_kernels(ctx, n_steps, C.c_void_p(out.ctypes.data)), ctx, "rcell_profile_kernels")
     return {n: float(v) for n, v in zip(PROFILE_NAMES, out) if v > 0}
+
+
+def rcell_get_rebuilds(ctx):
+    """Neighbour-list builds per cell since creation (uint64 array)."""
+    n = rcell_info(ctx)[0]
+    out = np.zeros(n, dtype=np.uint64)
+    _check(load().rcell_get_rebuilds(ctx, C.c_void_p(out.ctypes.data)), ctx, "rcell_get_rebuilds")
+    return out
+
+
+def rcell_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU in TFLOP/s."""
+    out = C.c_double(0.0)
+    st = load().rcell_fp32_peak(_stream_ptr(stream), C.byref(out))
+    if st != 0:
+        raise RCellError(st, "rcell_fp32_peak")
+    return out.value
 
 
 def rcell_checkpoint(ctx, cell: int) -> bytes:
