@@ -103,6 +103,9 @@ def lib():
         L.or_md_run.argtypes = [C.POINTER(Pot), C.POINTER(MD), C.c_int, D, D, D, C.c_int, I, C.c_uint32,
                                 C.POINTER(C.c_uint64), C.c_int, C.c_int, D, D, D]
         L.or_block_stats.argtypes = [C.c_int, D, C.c_int, D, D]
+        L.or_pk1_pairs.argtypes = [C.POINTER(Pot), C.c_int, C.c_int, D, D, D, C.c_int, I, D]
+        L.or_fire_minimize.argtypes = [C.POINTER(Pot), C.c_int, C.c_double, C.c_int, D, D, C.c_int, I, C.c_double,
+                                       C.c_double, C.c_double, C.c_int, I]
         L.or_hex8_geometry.argtypes = [D, D, D]
         L.or_hex8_F.argtypes = [D, D, D]
         L.or_hex8_fint.argtypes = [D, D, C.c_double, D, D, C.c_double, D]
@@ -224,6 +227,32 @@ def stress_inst(units, mass, v, W, H):
     s = np.zeros(6)
     lib().or_stress_inst(units, mass, v.shape[0], _dp(v), _dp(_f64(W, (3, 3))), _dp(_f64(H, (3, 3))), _dp(s))
     return s
+
+
+def pk1_pairs(pot, x, H, H0, bonds=None, units=0):
+    """Eq. PK1: first Piola-Kirchhoff stress (3,3) from the pair sum with the
+    reference separations R_ij = H0 H^{-1} r_ij; potential part, pressure units."""
+    x = _f64(x, (-1, 3))
+    b = np.zeros((0, 2), dtype=np.int32) if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32)
+    P = np.zeros((3, 3))
+    e = lib().or_pk1_pairs(C.byref(pot), units, x.shape[0], _dp(x), _dp(_f64(H, (3, 3))), _dp(_f64(H0, (3, 3))),
+                           b.shape[0], _ip(b), _dp(P))
+    if e:
+        raise OracleError(e, "pk1_pairs")
+    return P
+
+
+def fire_minimize(pot, x, H, mass, f_tol, dt0, dt_max, max_iter, bonds=None, units=0):
+    """Eq. CGPR1 by FIRE at fixed box: returns (minimised positions, force
+    evaluations before convergence or -1)."""
+    x = _f64(x, (-1, 3)).copy()
+    b = np.zeros((0, 2), dtype=np.int32) if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32)
+    it = C.c_int(0)
+    e = lib().or_fire_minimize(C.byref(pot), units, mass, x.shape[0], _dp(x), _dp(_f64(H, (3, 3))), b.shape[0],
+                               _ip(b), f_tol, dt0, dt_max, max_iter, C.byref(it))
+    if e:
+        raise OracleError(e, "fire_minimize")
+    return x, it.value
 
 
 def md_run(pot, md, x, v, H, bonds=None, cell=0, ev=0, n_steps=1, n_avg=0):

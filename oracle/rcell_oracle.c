@@ -814,3 +814,160 @@ void or_fe_update(int nn, const double *X, int ne, const int *conn, const double
     if (fint_out) memcpy(fint_out, fint, sizeof(double) * 3 * (size_t)nn);
     free(fint);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Molecular statics of an r-cell (Sec. 2.1, Eqs. CGPR1-CGPR3 and PK1).      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * First Piola-Kirchhoff stress from the pair sum (Eq. PK1 / Eq. CGPR2):
+ *   P = 1/(2 Omega_0) sum_{i != j} dE/dr_ij  r_ij (x) R_ij / r_ij,
+ * r_ij = x_j - x_i (current, nearest image within rc), R_ij = H0 H^{-1} r_ij
+ * the same separation in the reference box H0 (= H(0) S_ij), Omega_0 = det H0.
+ * dE/dr_ij is the derivative of the total energy with respect to the pair
+ * distance: the pair potential's for LJ / KG, and for Sutton-Chen the pair
+ * term plus both embedding contributions.  Kremer-Grest bonds (FENE + WCA)
+ * enter once per bond with their bond derivative.  Potential part only (no
+ * kinetic term); in the units of the unit system (GPa for metal).  Row-major
+ * P[3a+b] = P_ab.
+ */
+int or_pk1_pairs(const or_pot *P, int units, int n, const double *x, const double *H, const double *H0, int n_bonds,
+                 const int *bonds, double *Pk) {
+    or_plist L = {0, 0, 0};
+    int e = pairs_brute(n, x, H, P->rc, &L);
+    if (e) { free(L.p); return e; }
+    double Hi[9], M[9];
+    m3_inv(H, Hi);
+    m3_mul(H0, Hi, M);  /* R_ij = M r_ij */
+    double T[9] = {0};  /* sum over ordered pairs of dE/dr r (x) R / r */
+    int err = OR_OK;
+    or_bondmap B = {0, 0};
+    double *rho = NULL;
+    if (P->kind == OR_KG) {
+        err = bondmap_build(n, n_bonds, bonds, &B);
+        if (err) goto done;
+    }
+    if (P->kind == OR_SC) {
+        rho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        if (!rho) { err = OR_ENOMEM; goto done; }
+        for (long k = 0; k < L.n; k++) rho[L.p[k].i] += pow(P->sigma / sqrt(L.p[k].r2), P->m);
+    }
+    for (long k = 0; k < L.n; k++) {
+        const or_pair *q = &L.p[k];
+        if (P->kind == OR_KG && bonded(&B, q->i, q->j)) continue;
+        double r = sqrt(q->r2), dEdr;
+        if (P->kind == OR_SC) {
+            double ar = P->sigma / r;
+            dEdr = (P->eps / r) * (-P->n * pow(ar, P->n) +
+                                   0.5 * P->c * P->m * (1.0 / sqrt(rho[q->i]) + 1.0 / sqrt(rho[q->j])) * pow(ar, P->m));
+        } else {
+            double sr6 = pow(P->sigma * P->sigma / q->r2, 3);
+            dEdr = -24.0 * P->eps * (2.0 * sr6 * sr6 - sr6) / r;
+        }
+        double Rv[3];
+        m3_mv(M, q->d, Rv);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) T[3 * a + b] += dEdr * q->d[a] * Rv[b] / r;
+    }
+    if (P->kind == OR_KG) {
+        /* each bond once, with weight 2 against the ordered-pair half */
+        double rwca2 = pow(2.0, 1.0 / 3.0) * P->sigma * P->sigma, R02 = P->R0 * P->R0;
+        for (int b = 0; b < n_bonds; b++) {
+            int i = bonds[2 * b], j = bonds[2 * b + 1];
+            double dx[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]}, ds[3];
+            m3_mv(Hi, dx, ds);
+            double best = 1e300, bd[3] = {0, 0, 0};
+            for (int a0 = -1; a0 <= 1; a0++)
+                for (int a1 = -1; a1 <= 1; a1++)
+                    for (int a2 = -1; a2 <= 1; a2++) {
+                        double t[3] = {a0 - rint(ds[0]), a1 - rint(ds[1]), a2 - rint(ds[2])}, Ht[3];
+                        m3_mv(H, t, Ht);
+                        double dd[3] = {dx[0] + Ht[0], dx[1] + Ht[1], dx[2] + Ht[2]};
+                        double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                        if (r2 < best) { best = r2; bd[0] = dd[0]; bd[1] = dd[1]; bd[2] = dd[2]; }
+                    }
+            if (!(best < R02)) { err = OR_EBOND; goto done; }
+            double r = sqrt(best);
+            double dEdr = P->k_fene * r / (1.0 - best / R02);
+            if (best < rwca2) {
+                double sr6 = pow(P->sigma * P->sigma / best, 3);
+                dEdr += -24.0 * P->eps * (2.0 * sr6 * sr6 - sr6) / r;
+            }
+            double Rv[3];
+            m3_mv(M, bd, Rv);
+            for (int a = 0; a < 3; a++)
+                for (int c = 0; c < 3; c++) T[3 * a + c] += 2.0 * dEdr * bd[a] * Rv[c] / r;
+        }
+    }
+    {
+        double s = md_pconv(units) / (2.0 * m3_det(H0));
+        for (int k = 0; k < 9; k++) Pk[k] = s * T[k];
+    }
+done:
+    free(L.p);
+    free(B.start);
+    free(B.nbr);
+    free(rho);
+    return err;
+}
+
+/*
+ * Energy minimisation at fixed box (Eq. CGPR1: r_opt = argmin V from the
+ * guess r_ge) by FIRE, the fast inertial relaxation engine of Bitzek,
+ * Koskinen, Gaehler, Moseler and Gumbsch (Phys. Rev. Lett. 97, 170201, 2006).
+ * One iteration, with f = F(x) the forces, |.| norms over the whole cell:
+ *   stop if max_i |f_i| < f_tol (converged);
+ *   power p = f . v;
+ *   p > 0: n_pos += 1; v = (1 - alpha) v + alpha |v| f / |f|;
+ *          if n_pos > n_min: dt = min(f_inc dt, dt_max), alpha = f_alpha alpha;
+ *   p <= 0: n_pos = 0; v = 0; dt = f_dec dt; alpha = alpha_start;
+ *   v += dt f / m;  x += dt v   (semi-implicit Euler step).
+ * Starts from v = 0, dt = dt0, alpha = alpha_start.  Returns the number of
+ * force evaluations before convergence in *iters (-1: not converged within
+ * max_iter).  x is updated in place; the minimiser's constants are those of
+ * the cited paper (n_min 5, f_inc 1.1, f_dec 0.5, alpha_start 0.1, f_alpha 0.99).
+ */
+int or_fire_minimize(const or_pot *P, int units, double mass, int n, double *x, const double *H, int n_bonds,
+                     const int *bonds, double f_tol, double dt0, double dt_max, int max_iter, int *iters) {
+    const int n_min = 5;
+    const double f_inc = 1.1, f_dec = 0.5, alpha_start = 0.1, f_alpha = 0.99;
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *v = (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!f || !v) { free(f); free(v); return OR_ENOMEM; }
+    double fm = md_ftm2v(units) / mass, dt = dt0, alpha = alpha_start;
+    int n_pos = 0, err = OR_OK;
+    *iters = -1;
+    for (int it = 0; it < max_iter; it++) {
+        double W[9], pe;
+        err = or_forces(P, n, x, H, n_bonds, bonds, 1, f, W, &pe, NULL);
+        if (err) break;
+        double fmax2 = 0.0, p = 0.0, vv = 0.0, ff = 0.0;
+        for (int i = 0; i < n; i++) {
+            double f2 = f[3 * i] * f[3 * i] + f[3 * i + 1] * f[3 * i + 1] + f[3 * i + 2] * f[3 * i + 2];
+            if (f2 > fmax2) fmax2 = f2;
+        }
+        if (fmax2 < f_tol * f_tol) { *iters = it; break; }
+        for (int k = 0; k < 3 * n; k++) { p += f[k] * v[k]; vv += v[k] * v[k]; ff += f[k] * f[k]; }
+        if (p > 0.0) {
+            n_pos++;
+            double c = alpha * sqrt(vv) / sqrt(ff);
+            for (int k = 0; k < 3 * n; k++) v[k] = (1.0 - alpha) * v[k] + c * f[k];
+            if (n_pos > n_min) {
+                dt = fmin(f_inc * dt, dt_max);
+                alpha *= f_alpha;
+            }
+        } else {
+            n_pos = 0;
+            for (int k = 0; k < 3 * n; k++) v[k] = 0.0;
+            dt *= f_dec;
+            alpha = alpha_start;
+        }
+        for (int k = 0; k < 3 * n; k++) {
+            v[k] += dt * f[k] * fm;
+            x[k] += dt * v[k];
+        }
+    }
+    free(f);
+    free(v);
+    return err;
+}
