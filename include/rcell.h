@@ -195,6 +195,32 @@ int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
  * read-only cache.  Both give the same results up to summation order. */
 int rcell_set_staging(rcell_ctx *ctx, int staged);
 
+/* Molecular statics (Sec. 2.1, Eq. CGPR1): relax the atoms of every active
+ * cell without an error at fixed box to a local minimum of the potential
+ * energy, starting from the current positions (after rcell_set_deformation
+ * these are the Cauchy-Born guess F H(0) S of the previous configuration, the
+ * r^ge of the paper).  The minimiser is FIRE (Bitzek et al., Phys. Rev. Lett.
+ * 97, 170201, 2006; constants n_min 5, f_inc 1.1, f_dec 0.5, alpha 0.1,
+ * f_alpha 0.99), one FIRE state per cell, a semi-implicit Euler step with the
+ * atom mass: a cell stops once max_i |f_i| < f_tol (force units) at the start
+ * of an iteration.  dt0: initial step, dt_max: largest step (time units, dt_max
+ * >= dt0 > 0).  At most max_iter iterations.  iters_out (n_cells host ints, or
+ * NULL) receives each cell's number of moves before convergence (-1: not
+ * converged, or skipped).  Velocities are zero afterwards.  Synchronous.
+ * RC_EINVAL for bad arguments; cell errors as for rcell_run. */
+int rcell_minimize(rcell_ctx *ctx, int max_iter, double f_tol, double dt0, double dt_max, int *iters_out);
+
+/* Eq. PK1 / Eq. CGPR2 (Sec. 2.1): the first Piola-Kirchhoff stress of every
+ * cell from the pair sum over its current positions,
+ *   P_MD = 1/(2 Omega_0) sum_{i != j} dE/dr_ij r_ij (x) R_ij / r_ij,
+ * with R_ij = H(0) H^{-1} r_ij the separation in the reference box and
+ * Omega_0 = det H(0) (potential part only, no kinetic term); rotated to the FE
+ * frame, P = Q P_MD, and sigma = P F^T / J (tension-positive, Voigt xx yy zz
+ * xy xz yz with symmetrised off-diagonals).  Stress units as rcell_stress.
+ * sigma: n_cells x 6, P: n_cells x 9 row-major; either may be NULL; where:
+ * RC_HOST (synchronous, returns the first cell error) or RC_DEVICE. */
+int rcell_stress_static(rcell_ctx *ctx, double *sigma, double *P, int where);
+
 /* Neighbour-list builds per cell since creation (the initial build, one after
  * every deformation, and those the skin test triggered): counts receives
  * n_cells host values.  Synchronous.  RC_EINVAL for NULL arguments. */

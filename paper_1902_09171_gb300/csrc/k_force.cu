@@ -455,6 +455,96 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     }
 }
 
+// Eq. PK1 (Sec. 2.1): per cell, the sum over ordered pairs inside rc of
+// dE/dr_ij r_ij (x) R_ij / r_ij with R_ij = M r_ij, M = H(0) H^{-1} (upper
+// triangular, m[6] per cell: m00 m01 m02 m11 m12 m22), plus the Kremer-Grest
+// bonds, each seen from both ends.  FP32 per atom, FP64 per cell into
+// acc[9 c + 3 a + b]; the caller scales by 1 / (2 Omega_0).
+template <int POT, bool M6>
+__global__ void __launch_bounds__(RC_TILE) k_static_pk1(KParams p, KArrays a, int cur, const float *__restrict__ mcell,
+                                                        double *acc) {
+    const int t = blockIdx.x;
+    const int c = a.tile_cell[t];
+    if (a.status[c] != 0 || !a.active[c]) return;
+    __shared__ ShiftTab s_tab;
+    __shared__ float s_H[8];
+    rc_load_shifts(s_tab, s_H, a.Hf, c);
+    const float *m = mcell + 6 * c;
+    const float m00 = m[0], m01 = m[1], m02 = m[2], m11 = m[3], m12 = m[4], m22 = m[5];
+    const int n = a.cell_n[c], off = a.cell_off[c];
+    const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
+    const int g = off + li;
+    const float4 *__restrict__ X = cur ? a.x1 : a.x0;
+    const float4 *__restrict__ XG = (POT == RC_POT_SC) ? a.xr : X;
+    float T[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto add = [&](float gr, const float3 &d) {  // gr = dE/dr / r
+        const float R0 = fmaf(m00, d.x, fmaf(m01, d.y, m02 * d.z)), R1 = fmaf(m11, d.y, m12 * d.z), R2 = m22 * d.z;
+        const float gx = gr * d.x, gy = gr * d.y, gz = gr * d.z;
+        T[0] = fmaf(gx, R0, T[0]); T[1] = fmaf(gx, R1, T[1]); T[2] = fmaf(gx, R2, T[2]);
+        T[3] = fmaf(gy, R0, T[3]); T[4] = fmaf(gy, R1, T[4]); T[5] = fmaf(gy, R2, T[5]);
+        T[6] = fmaf(gz, R0, T[6]); T[7] = fmaf(gz, R1, T[7]); T[8] = fmaf(gz, R2, T[8]);
+    };
+    if (li < n) {
+        const float4 xi = XG[g];
+        const int nn = a.nnb[g];
+        const int4 *__restrict__ nb =
+            reinterpret_cast<const int4 *>(a.nbr) + (size_t)t * (p.max_nb / 4) * RC_TILE + threadIdx.x;
+        const float rc2 = p.rc2;
+        if (POT == RC_POT_SC) {
+            const float a2 = p.sigma * p.sigma, hm = 0.5f * p.sc_m, hn = 0.5f * p.sc_n;
+            const float cm2 = 0.5f * p.sc_c * p.sc_m, eps = p.eps, sc_n = p.sc_n, sig = p.sigma;
+            for_each_neighbor<1>(nb, nn, 0, GlobalSrc{XG}, xi, s_tab, [&](const float4 &xj, const float3 &d) {
+                const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                if (r2 < rc2) {
+                    const float ir2 = __fdividef(1.0f, r2), ar2 = a2 * ir2;
+                    float arm, arn;
+                    if (M6) {
+                        arm = ar2 * ar2 * ar2;
+                        arn = arm * ar2 * (sig * rsqrtf(r2));
+                    } else {
+                        arm = powf(ar2, hm);
+                        arn = powf(ar2, hn);
+                    }
+                    add(eps * ir2 * fmaf(cm2 * (xi.w + xj.w), arm, -sc_n * arn), d);
+                }
+            });
+        } else {
+            const float s2 = p.sigma * p.sigma, c24 = 24.0f * p.eps;
+            for_each_neighbor<1>(nb, nn, 0, GlobalSrc{XG}, xi, s_tab, [&](const float4 &, const float3 &d) {
+                const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                if (r2 < rc2) {
+                    const float ir2 = __fdividef(1.0f, r2), sr2 = s2 * ir2, sr6 = sr2 * sr2 * sr2;
+                    add(-c24 * ir2 * sr6 * (2.0f * sr6 - 1.0f), d);
+                }
+            });
+        }
+        if (POT == RC_POT_KG) {
+            const int4 pr = a.partner[g];
+            const int q[4] = {pr.x, pr.y, pr.z, pr.w};
+            const float *Hi = a.Hif + 8 * c;
+#pragma unroll
+            for (int b = 0; b < RC_MAX_BONDS; b++) {
+                if (q[b] < 0) continue;
+                const float4 xj = X[off + q[b]];
+                const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
+                const float f2 = Hi[5] * ez, f1 = Hi[3] * ey + Hi[4] * ez, f0 = Hi[0] * ex + Hi[1] * ey + Hi[2] * ez;
+                const int n0 = -(int)rintf(f0), n1 = -(int)rintf(f1), n2 = -(int)rintf(f2);
+                if (n0 < -1 || n0 > 1 || n1 < -1 || n1 > 1 || n2 < -1 || n2 > 1) continue;
+                const float3 dd = rc_disp(xi, xj, s_tab, (n0 + 1) + 3 * (n1 + 1) + 9 * (n2 + 1));
+                const float r2 = fmaf(dd.x, dd.x, fmaf(dd.y, dd.y, dd.z * dd.z));
+                if (!(r2 < p.R02)) continue;
+                float gr = p.k_fene / (1.0f - r2 / p.R02);
+                if (r2 < p.wca2) {
+                    const float sr2 = p.sigma * p.sigma / r2, sr6 = sr2 * sr2 * sr2;
+                    gr -= 24.0f * p.eps * sr6 * (2.0f * sr6 - 1.0f) / r2;
+                }
+                add(gr, dd);
+            }
+        }
+    }
+    block_reduce_add<9, RC_TILE>(T, acc + 9 * c);
+}
+
 template <class K>
 void set_smem(K kernel, int bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -557,5 +647,17 @@ void rc_launch_force(const KParams &p, const KArrays &a, int cur, int n_tiles, i
     } else {
         if (st) launch_force_pot<RC_POT_LJ, false, true>(p, a, cur, n_tiles, tpa, mode, slot, step_index, smem, s);
         else launch_force_pot<RC_POT_LJ, false, false>(p, a, cur, n_tiles, tpa, mode, slot, step_index, 0, s);
+    }
+}
+
+void rc_launch_static_pk1(const KParams &p, const KArrays &a, int cur, int n_tiles, const float *mcell, double *acc,
+                          cudaStream_t s) {
+    if (p.pot == RC_POT_SC) {
+        if (p.sc_m == 6.0f && p.sc_n == 9.0f) k_static_pk1<RC_POT_SC, true><<<n_tiles, RC_TILE, 0, s>>>(p, a, cur, mcell, acc);
+        else k_static_pk1<RC_POT_SC, false><<<n_tiles, RC_TILE, 0, s>>>(p, a, cur, mcell, acc);
+    } else if (p.pot == RC_POT_KG) {
+        k_static_pk1<RC_POT_KG, false><<<n_tiles, RC_TILE, 0, s>>>(p, a, cur, mcell, acc);
+    } else {
+        k_static_pk1<RC_POT_LJ, false><<<n_tiles, RC_TILE, 0, s>>>(p, a, cur, mcell, acc);
     }
 }

@@ -158,6 +158,14 @@ __device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, co
                        (xj.z + sa.z) - (xi.z - sb.z));
 }
 
+// per-cell state of the FIRE minimiser (k_fire.cu)
+struct FireState {
+    double *acc;      // [cell][4]: f.v, |v|^2, |f|^2, pad
+    unsigned *fmax2;  // max |f_i|^2 as float bits
+    float *dt, *alpha, *mixa, *mixb;
+    int *npos, *done, *iters, *it, *zero;
+};
+
 // host-side launchers (defined in the kernel translation units)
 void rc_launch_sort(const KParams &p, const KArrays &a, int cur, int n_cells, cudaStream_t s);
 void rc_launch_nlist(const KParams &p, const KArrays &a, int cur, int n_tiles, cudaStream_t s);
@@ -176,6 +184,17 @@ void rc_launch_remap(const KArrays &a, const double *dR, int cur, int n_tiles, c
 void rc_launch_stress(const double *series, int n_avg, int series_cap, const double *H, const double *Q,
                       const double *F, double pconv, double *rot_scratch, double *sig_fem, double *sig_se,
                       double *sig_md, double *P, int n_cells, cudaStream_t s);
+void rc_launch_static_pk1(const KParams &p, const KArrays &a, int cur, int n_tiles, const float *mcell, double *acc,
+                          cudaStream_t s);
+void rc_launch_fire_init(const FireState &s, const int *status, const int *active, int n_cells, float dt0,
+                         cudaStream_t st);
+void rc_launch_fire_zero_v(const KArrays &a, const FireState &s, int n_tiles, int all_cells, cudaStream_t st);
+void rc_launch_fire_iteration(const KParams &p, const KArrays &a, int cur, const FireState &s, int n_tiles, int n_cells,
+                              float f_tol, float dt_max, int *n_left, cudaStream_t st);
+void rc_launch_static_prep(const double *H, const double *H0, float *mcell, double *acc, int n_cells,
+                           cudaStream_t st);
+void rc_launch_static_finish(const double *acc, const double *H0, const double *Q, const double *F, double pconv,
+                             double *P, double *sig, const int *status, int n_cells, cudaStream_t st);
 void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s);
 
 // finite elements (k_fe.cu)

@@ -51,6 +51,11 @@ struct rcell_ctx {
     int max_cell = 0;    // largest cell of the batch (atoms)
     int staged = 0;      // stage whole cells in shared memory (when they fit) -- off by default
     long launches_last = 0;
+    // molecular statics (allocated on first use)
+    FireState fire{};
+    int *d_fire_left = nullptr;
+    float *d_mcell = nullptr;
+    double *d_pk_acc = nullptr;
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, int, int, int>, long> graph_launches;
     std::string err = "ok";
@@ -602,6 +607,75 @@ int rcell_set_tuning(rcell_ctx *c, int threads_per_atom, int use_graphs) {
         c->tpa = threads_per_atom;
     }
     if (use_graphs >= 0) c->use_graphs = use_graphs ? 1 : 0;
+    return RC_OK;
+}
+
+int rcell_minimize(rcell_ctx *c, int max_iter, double f_tol, double dt0, double dt_max, int *iters_out) {
+    if (!c || max_iter < 0 || !(f_tol > 0) || !(dt0 > 0) || !(dt_max >= dt0)) return RC_EINVAL;
+    const int nc = c->n_cells;
+    if (!c->fire.acc) {
+        auto &L = c->allocs;
+        FireState &f = c->fire;
+        CKC(c, dalloc(L, &f.acc, 4 * (size_t)nc));
+        CKC(c, dalloc(L, &f.fmax2, nc));
+        CKC(c, dalloc(L, &f.dt, nc));
+        CKC(c, dalloc(L, &f.alpha, nc));
+        CKC(c, dalloc(L, &f.mixa, nc));
+        CKC(c, dalloc(L, &f.mixb, nc));
+        CKC(c, dalloc(L, &f.npos, nc));
+        CKC(c, dalloc(L, &f.done, nc));
+        CKC(c, dalloc(L, &f.iters, nc));
+        CKC(c, dalloc(L, &f.it, nc));
+        CKC(c, dalloc(L, &f.zero, nc));
+        CKC(c, dalloc(L, &c->d_fire_left, 1));
+    }
+    rc_launch_fire_init(c->fire, c->ka.status, c->ka.active, nc, (float)dt0, c->stream);
+    rc_launch_fire_zero_v(c->ka, c->fire, c->n_tiles, 0, c->stream);
+    // iterations in batches between convergence checks: forces (MODE_EVAL, after the
+    // list and density kernels), then the FIRE power / control / move kernels
+    const int batch = 32;
+    for (int it0 = 0; it0 < max_iter; it0 += batch) {
+        CKC(c, cudaMemsetAsync(c->d_fire_left, 0, sizeof(int), c->stream));
+        const int nb = std::min(batch, max_iter - it0);
+        for (int k = 0; k < nb; k++) {  // the last iteration of the batch counts the cells still moving
+            enqueue_step(c, MODE_EVAL, -1, 0);
+            rc_launch_fire_iteration(c->kp, c->ka, c->cur, c->fire, c->n_tiles, nc, (float)f_tol, (float)dt_max,
+                                     k == nb - 1 ? c->d_fire_left : nullptr, c->stream);
+        }
+        CKC(c, cudaGetLastError());
+        int left = 0;
+        CKC(c, cudaMemcpyAsync(&left, c->d_fire_left, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CKC(c, cudaStreamSynchronize(c->stream));
+        if (left == 0) break;
+    }
+    rc_launch_fire_zero_v(c->ka, c->fire, c->n_tiles, 1, c->stream);
+    CKC(c, cudaGetLastError());
+    if (iters_out) {
+        CKC(c, cudaMemcpyAsync(iters_out, c->fire.iters, sizeof(int) * nc, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CKC(c, cudaStreamSynchronize(c->stream));
+    return first_status(c);
+}
+
+int rcell_stress_static(rcell_ctx *c, double *sigma, double *P, int where) {
+    if (!c) return RC_EINVAL;
+    const int nc = c->n_cells;
+    if (!c->d_mcell) {
+        CKC(c, dalloc(c->allocs, &c->d_mcell, 6 * (size_t)nc));
+        CKC(c, dalloc(c->allocs, &c->d_pk_acc, 9 * (size_t)nc));
+    }
+    rc_launch_static_prep(c->d_H, c->d_H0, c->d_mcell, c->d_pk_acc, nc, c->stream);
+    rc_launch_sort(c->kp, c->ka, c->cur, nc, c->stream);
+    rc_launch_nlist(c->kp, c->ka, c->cur, c->n_tiles, c->stream);
+    if (c->kp.pot == RC_POT_SC) rc_launch_density(c->kp, c->ka, c->cur, c->n_tiles, 1, 0, c->stream);
+    rc_launch_static_pk1(c->kp, c->ka, c->cur, c->n_tiles, c->d_mcell, c->d_pk_acc, c->stream);
+    rc_launch_static_finish(c->d_pk_acc, c->d_H0, c->d_Q, c->d_F, pconv_of(c->prm.units), c->d_P, c->d_sig_fem,
+                            c->ka.status, nc, c->stream);
+    CKC(c, cudaGetLastError());
+    const cudaMemcpyKind kind = where == RC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (sigma) CKC(c, cudaMemcpyAsync(sigma, c->d_sig_fem, sizeof(double) * 6 * nc, kind, c->stream));
+    if (P) CKC(c, cudaMemcpyAsync(P, c->d_P, sizeof(double) * 9 * nc, kind, c->stream));
+    if (where == RC_HOST) return first_status(c);
     return RC_OK;
 }
 

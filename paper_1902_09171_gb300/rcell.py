@@ -47,7 +47,7 @@ class rcell_init(C.Structure):
 _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
-           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
+           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_minimize", "rcell_stress_static", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
            "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
@@ -82,6 +82,8 @@ def load(path: str | None = None):
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
         "rcell_fp32_peak": ([vp, vp], C.c_int),
         "rcell_get_rebuilds": ([vp, vp], C.c_int),
+        "rcell_minimize": ([vp, C.c_int, C.c_double, C.c_double, C.c_double, vp], C.c_int),
+        "rcell_stress_static": ([vp, vp, vp, C.c_int], C.c_int),
         "rcell_checkpoint": ([vp, C.c_int, vp, C.POINTER(C.c_size_t)], C.c_int),
         "rcell_restore": ([vp, C.c_int, vp, C.c_size_t], C.c_int),
         "rcell_stress_reduce_static": ([vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -276,6 +278,28 @@ def rcell_profile_kernels(ctx, n_steps: int):
     out = np.zeros(8)
     _check(load().rcell_profile_kernels(ctx, n_steps, C.c_void_p(out.ctypes.data)), ctx, "rcell_profile_kernels")
     return {n: float(v) for n, v in zip(PROFILE_NAMES, out) if v > 0}
+
+
+def rcell_minimize(ctx, max_iter, f_tol, dt0, dt_max):
+    """FIRE relaxation at fixed box (Eq. CGPR1); returns per-cell move counts (-1: not converged)."""
+    n = rcell_info(ctx)[0]
+    it = np.zeros(n, dtype=np.int32)
+    _check(load().rcell_minimize(ctx, int(max_iter), float(f_tol), float(dt0), float(dt_max),
+                                 C.c_void_p(it.ctypes.data)), ctx, "rcell_minimize")
+    return it
+
+
+def rcell_stress_static(ctx, sigma=None, P=None):
+    """Eq. PK1 stress of every cell from the pair sum: fills / returns (sigma (n,6), P (n,3,3)), host
+    numpy arrays or CUDA tensors."""
+    n = rcell_info(ctx)[0]
+    if sigma is None and P is None:
+        sigma, P = np.zeros((n, 6)), np.zeros((n, 3, 3))
+    ps, ws, ks = _arr_ptr(sigma) if sigma is not None else (None, RC_HOST, None)
+    pp, wp, kp = _arr_ptr(P) if P is not None else (None, ws, None)
+    where = ws if sigma is not None else wp
+    _check(load().rcell_stress_static(ctx, ps, pp, where), ctx, "rcell_stress_static")
+    return sigma, P
 
 
 def rcell_get_rebuilds(ctx):
