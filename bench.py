@@ -426,6 +426,79 @@ def run_kg_bar(args):
     return out
 
 
+def run_kg_statics(args):
+    """The paper's molecular-statics r-cell route (Sec. 2.1, Eqs. CGPR1-CGPR3, PK1)
+    on amorphous Kremer-Grest cells: 32 cells of 5000 beads, quenched to a local
+    energy minimum; one bench step = one load increment of uniaxial stretch (0.5 %)
+    through rcell_set_deformation (the Cauchy-Born guess), FIRE relaxation of every
+    cell to max |f| < 1e-2 and the pair-sum first Piola-Kirchhoff stress."""
+    import torch
+
+    import oracle
+    from paper_1902_09171_gb300 import build, rcell
+    build.build()
+    rcell.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n_cells, f_tol, dt0, dt_max, dmax, max_iter = 32, 1e-2, 0.005, 0.05, 0.05, 50000
+    cells = inputs.kg_cells(n_cells, 100, 50, 0.85, seed=400, n_distinct=4)
+    soft = rcell.params_kg(tau=0.5, kT=1.0, dt=0.002, seed=4, max_step=0.02)
+    ctx = rcell.rcell_create(soft, cells, stream=stream)
+    rcell.rcell_run(ctx, 1000, 0)
+    glass = []
+    for k, c in enumerate(cells):
+        x, _, _ = rcell.rcell_get_atoms(ctx, k, len(c["x0"]))
+        glass.append(dict(H0=c["H0"], x0=x, v0=np.zeros_like(x), bonds=c["bonds"]))
+    rcell.rcell_destroy(ctx)
+    prm = rcell.params_kg(skin=0.3)
+    ctx = rcell.rcell_create(prm, glass, stream=stream)
+    rcell.rcell_minimize(ctx, max_iter, f_tol, dt0, dt_max, dmax)  # the unstrained minimum
+    n_atoms = np.array([len(c["x0"]) for c in glass])
+    sig = torch.zeros((n_cells, 6), dtype=torch.float64, device="cuda")
+
+    def increment(k):
+        eps = 0.005 * (k + 1)
+        rcell.rcell_set_deformation(ctx, np.tile(np.diag([1.0 + eps, 1.0, 1.0]), (n_cells, 1, 1)))
+        it = rcell.rcell_minimize(ctx, max_iter, f_tol, dt0, dt_max, dmax)
+        rcell.rcell_stress_static(ctx, sig)
+        return it
+
+    for k in range(args.warmup):
+        increment(k)
+    torch.cuda.synchronize()
+    work, ms, iters = 0, 0.0, []
+    for k in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it = increment(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        iters.append(int(it.max()))
+        work += int((n_atoms * (np.maximum(it, 0) + 1)).sum())  # force evaluations of cells still moving
+    st = rcell.rcell_sync(ctx)
+    value = work / (ms / 1e3)
+    # oracle on a bounded sample: one cell, the same relaxation, at most 30 iterations
+    pot = oracle.pot_kg()
+    H, _, _ = rcell.rcell_get_box(ctx, 0)
+    x0 = rcell.rcell_get_atoms(ctx, 0, int(n_atoms[0]))[0] @ np.diag([1.005, 1.0, 1.0]).T
+    t0 = time.perf_counter()
+    oracle.fire_minimize(pot, x0, np.diag([1.005, 1.0, 1.0]) @ H, 1.0, f_tol, dt0, dt_max, 30,
+                         bonds=glass[0]["bonds"], units=1, dmax=dmax)
+    cpu_s = time.perf_counter() - t0
+    out = {"metric": "atom force-evaluations/s, batched r-cell molecular statics (Kremer-Grest glass)",
+           "value": value, "unit": "atom-evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "status": rcell.STATUS[st], "data": "synthetic",
+           "dtype": "f32 (pair math) / f64 (cell sums, stress)",
+           "config": {"workload": f"kg_statics_{n_cells}x5000", "f_tol": f_tol, "dmax": dmax, "strain_per_increment": 0.005,
+                      "fire_iterations_per_increment": iters},
+           "fe_load_steps_per_s": args.steps / (ms / 1e3),
+           "cpu_baseline": {"value": int(n_atoms[0]) * 31 / cpu_s, "unit": "atom-evaluations/s", "cores": 1,
+                            "kind": "oracle", "sample": "one 5000-bead cell, 30 FIRE iterations, FP64"}}
+    rcell.rcell_destroy(ctx)
+    return out
+
+
 def run_surrogate_fe(args):
     """The learned surrogate against plain r-cell MD on an FE bar of Kremer-Grest
     r-cells (5000 beads each): S1 data generation through batched r-cells, BF16
@@ -495,7 +568,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe"])
+    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics"])
     ap.add_argument("--kg-cells", type=int, default=64)
     ap.add_argument("--pushoff", type=int, default=60)
     ap.add_argument("--paths", type=int, default=1024)
@@ -511,7 +584,8 @@ def main():
     if args.workload != "copper_bar":
         if args.md_steps == MD_STEPS and args.workload == "kg_bar":
             args.md_steps = 1000
-        out = run_kg_bar(args) if args.workload == "kg_bar" else run_surrogate_fe(args)
+        run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "kg_statics": run_kg_statics}[args.workload]
+        out = run(args)
         print(json.dumps(out))
         return
     out = run_ours(args)

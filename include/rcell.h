@@ -204,11 +204,13 @@ int rcell_set_staging(rcell_ctx *ctx, int staged);
  * f_alpha 0.99), one FIRE state per cell, a semi-implicit Euler step with the
  * atom mass: a cell stops once max_i |f_i| < f_tol (force units) at the start
  * of an iteration.  dt0: initial step, dt_max: largest step (time units, dt_max
- * >= dt0 > 0).  At most max_iter iterations.  iters_out (n_cells host ints, or
+ * >= dt0 > 0); dmax > 0 caps every atom's move per iteration (its velocity is
+ * scaled down; <= 0: no cap).  At most max_iter iterations.  iters_out (n_cells host ints, or
  * NULL) receives each cell's number of moves before convergence (-1: not
  * converged, or skipped).  Velocities are zero afterwards.  Synchronous.
  * RC_EINVAL for bad arguments; cell errors as for rcell_run. */
-int rcell_minimize(rcell_ctx *ctx, int max_iter, double f_tol, double dt0, double dt_max, int *iters_out);
+int rcell_minimize(rcell_ctx *ctx, int max_iter, double f_tol, double dt0, double dt_max, double dmax,
+                   int *iters_out);
 
 /* Eq. PK1 / Eq. CGPR2 (Sec. 2.1): the first Piola-Kirchhoff stress of every
  * cell from the pair sum over its current positions,

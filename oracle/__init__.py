@@ -105,7 +105,7 @@ def lib():
         L.or_block_stats.argtypes = [C.c_int, D, C.c_int, D, D]
         L.or_pk1_pairs.argtypes = [C.POINTER(Pot), C.c_int, C.c_int, D, D, D, C.c_int, I, D]
         L.or_fire_minimize.argtypes = [C.POINTER(Pot), C.c_int, C.c_double, C.c_int, D, D, C.c_int, I, C.c_double,
-                                       C.c_double, C.c_double, C.c_int, I]
+                                       C.c_double, C.c_double, C.c_double, C.c_int, I]
         L.or_hex8_geometry.argtypes = [D, D, D]
         L.or_hex8_F.argtypes = [D, D, D]
         L.or_hex8_fint.argtypes = [D, D, C.c_double, D, D, C.c_double, D]
@@ -242,14 +242,14 @@ def pk1_pairs(pot, x, H, H0, bonds=None, units=0):
     return P
 
 
-def fire_minimize(pot, x, H, mass, f_tol, dt0, dt_max, max_iter, bonds=None, units=0):
-    """Eq. CGPR1 by FIRE at fixed box: returns (minimised positions, force
-    evaluations before convergence or -1)."""
+def fire_minimize(pot, x, H, mass, f_tol, dt0, dt_max, max_iter, bonds=None, units=0, dmax=0.0):
+    """Eq. CGPR1 by FIRE at fixed box (per-atom move cap dmax, <= 0: none):
+    returns (minimised positions, moves before convergence or -1)."""
     x = _f64(x, (-1, 3)).copy()
     b = np.zeros((0, 2), dtype=np.int32) if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32)
     it = C.c_int(0)
     e = lib().or_fire_minimize(C.byref(pot), units, mass, x.shape[0], _dp(x), _dp(_f64(H, (3, 3))), b.shape[0],
-                               _ip(b), f_tol, dt0, dt_max, max_iter, C.byref(it))
+                               _ip(b), f_tol, dt0, dt_max, dmax, max_iter, C.byref(it))
     if e:
         raise OracleError(e, "fire_minimize")
     return x, it.value

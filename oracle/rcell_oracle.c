@@ -921,14 +921,16 @@ done:
  *   p > 0: n_pos += 1; v = (1 - alpha) v + alpha |v| f / |f|;
  *          if n_pos > n_min: dt = min(f_inc dt, dt_max), alpha = f_alpha alpha;
  *   p <= 0: n_pos = 0; v = 0; dt = f_dec dt; alpha = alpha_start;
- *   v += dt f / m;  x += dt v   (semi-implicit Euler step).
+ *   v += dt f / m;  x += dt v   (semi-implicit Euler step), where an atom whose
+ *   move dt |v| would exceed dmax (> 0) has its velocity scaled to move dmax
+ *   (a per-atom displacement cap, dmax <= 0: none).
  * Starts from v = 0, dt = dt0, alpha = alpha_start.  Returns the number of
  * force evaluations before convergence in *iters (-1: not converged within
  * max_iter).  x is updated in place; the minimiser's constants are those of
  * the cited paper (n_min 5, f_inc 1.1, f_dec 0.5, alpha_start 0.1, f_alpha 0.99).
  */
 int or_fire_minimize(const or_pot *P, int units, double mass, int n, double *x, const double *H, int n_bonds,
-                     const int *bonds, double f_tol, double dt0, double dt_max, int max_iter, int *iters) {
+                     const int *bonds, double f_tol, double dt0, double dt_max, double dmax, int max_iter, int *iters) {
     const int n_min = 5;
     const double f_inc = 1.1, f_dec = 0.5, alpha_start = 0.1, f_alpha = 0.99;
     double *f = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -962,9 +964,14 @@ int or_fire_minimize(const or_pot *P, int units, double mass, int n, double *x, 
             dt *= f_dec;
             alpha = alpha_start;
         }
-        for (int k = 0; k < 3 * n; k++) {
-            v[k] += dt * f[k] * fm;
-            x[k] += dt * v[k];
+        for (int i = 0; i < n; i++) {
+            for (int a = 0; a < 3; a++) v[3 * i + a] += dt * f[3 * i + a] * fm;
+            double s2 = dt * dt * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+            if (dmax > 0.0 && s2 > dmax * dmax) {
+                double sc = dmax / sqrt(s2);
+                for (int a = 0; a < 3; a++) v[3 * i + a] *= sc;
+            }
+            for (int a = 0; a < 3; a++) x[3 * i + a] += dt * v[3 * i + a];
         }
     }
     free(f);

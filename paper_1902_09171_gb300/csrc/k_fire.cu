@@ -8,7 +8,8 @@
 // p = f . v; p > 0: n_pos += 1, v = (1 - alpha) v + alpha |v| f / |f|, and
 // after more than 5 such steps dt = min(1.1 dt, dt_max), alpha = 0.99 alpha;
 // p <= 0: n_pos = 0, v = 0, dt = dt / 2, alpha = 0.1; then v += dt f / m,
-// x += dt v.  Kernels: k_fire_power (per-cell p, |v|^2, |f|^2, max |f|^2),
+// x += dt v, an atom whose move would exceed dmax (> 0) having its velocity
+// scaled to move dmax.  Kernels: k_fire_power (per-cell p, |v|^2, |f|^2, max |f|^2),
 // k_fire_control (per cell), k_fire_move (per atom).
 #include "rc_internal.cuh"
 
@@ -113,7 +114,7 @@ __global__ void k_fire_control(FireState s, int n_cells, float f_tol2, float dt_
     if (n_left) atomicAdd(n_left, 1);
 }
 
-__global__ void __launch_bounds__(RC_TILE) k_fire_move(KParams p, KArrays a, int cur, FireState s) {
+__global__ void __launch_bounds__(RC_TILE) k_fire_move(KParams p, KArrays a, int cur, FireState s, float dmax) {
     const int t = blockIdx.x, c = a.tile_cell[t];
     if (s.done[c]) return;
     const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
@@ -133,6 +134,13 @@ __global__ void __launch_bounds__(RC_TILE) k_fire_move(KParams p, KArrays a, int
     v.x = fmaf(h, f.x, v.x);
     v.y = fmaf(h, f.y, v.y);
     v.z = fmaf(h, f.z, v.z);
+    const float s2 = dt * dt * (v.x * v.x + v.y * v.y + v.z * v.z);
+    if (dmax > 0.0f && s2 > dmax * dmax) {  // per-atom move cap
+        const float sc = dmax * rsqrtf(s2);
+        v.x *= sc;
+        v.y *= sc;
+        v.z *= sc;
+    }
     a.v[g] = v;
     float4 *X = cur ? a.x1 : a.x0;
     float4 x = X[g];
@@ -214,10 +222,10 @@ void rc_launch_fire_zero_v(const KArrays &a, const FireState &s, int n_tiles, in
 }
 
 void rc_launch_fire_iteration(const KParams &p, const KArrays &a, int cur, const FireState &s, int n_tiles, int n_cells,
-                              float f_tol, float dt_max, int *n_left, cudaStream_t st) {
+                              float f_tol, float dt_max, float dmax, int *n_left, cudaStream_t st) {
     k_fire_power<<<n_tiles, RC_TILE, 0, st>>>(a, s);
     k_fire_control<<<(n_cells + 127) / 128, 128, 0, st>>>(s, n_cells, f_tol * f_tol, dt_max, n_left);
-    k_fire_move<<<n_tiles, RC_TILE, 0, st>>>(p, a, cur, s);
+    k_fire_move<<<n_tiles, RC_TILE, 0, st>>>(p, a, cur, s, dmax);
 }
 
 void rc_launch_static_prep(const double *H, const double *H0, float *mcell, double *acc, int n_cells,

@@ -190,7 +190,7 @@ void rc_launch_fire_init(const FireState &s, const int *status, const int *activ
                          cudaStream_t st);
 void rc_launch_fire_zero_v(const KArrays &a, const FireState &s, int n_tiles, int all_cells, cudaStream_t st);
 void rc_launch_fire_iteration(const KParams &p, const KArrays &a, int cur, const FireState &s, int n_tiles, int n_cells,
-                              float f_tol, float dt_max, int *n_left, cudaStream_t st);
+                              float f_tol, float dt_max, float dmax, int *n_left, cudaStream_t st);
 void rc_launch_static_prep(const double *H, const double *H0, float *mcell, double *acc, int n_cells,
                            cudaStream_t st);
 void rc_launch_static_finish(const double *acc, const double *H0, const double *Q, const double *F, double pconv,

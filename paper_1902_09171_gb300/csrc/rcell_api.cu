@@ -610,7 +610,8 @@ int rcell_set_tuning(rcell_ctx *c, int threads_per_atom, int use_graphs) {
     return RC_OK;
 }
 
-int rcell_minimize(rcell_ctx *c, int max_iter, double f_tol, double dt0, double dt_max, int *iters_out) {
+int rcell_minimize(rcell_ctx *c, int max_iter, double f_tol, double dt0, double dt_max, double dmax,
+                   int *iters_out) {
     if (!c || max_iter < 0 || !(f_tol > 0) || !(dt0 > 0) || !(dt_max >= dt0)) return RC_EINVAL;
     const int nc = c->n_cells;
     if (!c->fire.acc) {
@@ -640,7 +641,7 @@ int rcell_minimize(rcell_ctx *c, int max_iter, double f_tol, double dt0, double 
         for (int k = 0; k < nb; k++) {  // the last iteration of the batch counts the cells still moving
             enqueue_step(c, MODE_EVAL, -1, 0);
             rc_launch_fire_iteration(c->kp, c->ka, c->cur, c->fire, c->n_tiles, nc, (float)f_tol, (float)dt_max,
-                                     k == nb - 1 ? c->d_fire_left : nullptr, c->stream);
+                                     (float)dmax, k == nb - 1 ? c->d_fire_left : nullptr, c->stream);
         }
         CKC(c, cudaGetLastError());
         int left = 0;

@@ -82,7 +82,7 @@ def load(path: str | None = None):
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
         "rcell_fp32_peak": ([vp, vp], C.c_int),
         "rcell_get_rebuilds": ([vp, vp], C.c_int),
-        "rcell_minimize": ([vp, C.c_int, C.c_double, C.c_double, C.c_double, vp], C.c_int),
+        "rcell_minimize": ([vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, vp], C.c_int),
         "rcell_stress_static": ([vp, vp, vp, C.c_int], C.c_int),
         "rcell_checkpoint": ([vp, C.c_int, vp, C.POINTER(C.c_size_t)], C.c_int),
         "rcell_restore": ([vp, C.c_int, vp, C.c_size_t], C.c_int),
@@ -280,11 +280,11 @@ def rcell_profile_kernels(ctx, n_steps: int):
     return {n: float(v) for n, v in zip(PROFILE_NAMES, out) if v > 0}
 
 
-def rcell_minimize(ctx, max_iter, f_tol, dt0, dt_max):
+def rcell_minimize(ctx, max_iter, f_tol, dt0, dt_max, dmax=0.0):
     """FIRE relaxation at fixed box (Eq. CGPR1); returns per-cell move counts (-1: not converged)."""
     n = rcell_info(ctx)[0]
     it = np.zeros(n, dtype=np.int32)
-    _check(load().rcell_minimize(ctx, int(max_iter), float(f_tol), float(dt0), float(dt_max),
+    _check(load().rcell_minimize(ctx, int(max_iter), float(f_tol), float(dt0), float(dt_max), float(dmax),
                                  C.c_void_p(it.ctypes.data)), ctx, "rcell_minimize")
     return it
 

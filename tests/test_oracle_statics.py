@@ -85,3 +85,23 @@ def test_fire_stops_at_once_when_already_relaxed_and_reports_non_convergence():
     x0 = inputs.jitter(X, 0.05, 32)
     _, it2 = oracle.fire_minimize(lj_cu(), x0, H0, 63.546, 1e-12, 2e-3, 2e-2, 3)
     assert it2 == -1
+
+
+def test_fire_move_cap_limits_every_atom_displacement():
+    # a melt straight from the generator has overlaps and large forces: one
+    # iteration with the cap moves no atom by more than dmax, and the cap is
+    # only active where the uncapped move would be larger
+    x0, H, bonds = inputs.kg_melt(6, 20, 0.85, seed=33, pushoff_iters=20)
+    pot = oracle.pot_kg()
+    x1, _ = oracle.fire_minimize(pot, x0, H, 1.0, 1e-12, 0.005, 0.05, 1, bonds=bonds, units=1, dmax=0.01)
+    d = np.linalg.norm(x1 - x0, axis=1)
+    assert d.max() <= 0.01 * (1 + 1e-12)
+    x2, _ = oracle.fire_minimize(pot, x0, H, 1.0, 1e-12, 0.005, 0.05, 1, bonds=bonds, units=1)
+    d2 = np.linalg.norm(x2 - x0, axis=1)
+    capped = d2 > 0.01
+    assert capped.any() and np.allclose(d[~capped], d2[~capped], rtol=0, atol=1e-15)
+    # a capped relaxation of the melt ends at a minimum without breaking bonds
+    xm, it = oracle.fire_minimize(pot, x0, H, 1.0, 1e-6, 0.005, 0.05, 20000, bonds=bonds, units=1, dmax=0.05)
+    assert it > 0
+    f, _, _ = oracle.forces(pot, xm, H, bonds=bonds)
+    assert np.sqrt((f ** 2).sum(1)).max() < 1e-6
