@@ -499,6 +499,65 @@ def run_kg_statics(args):
     return out
 
 
+def run_surrogate_train(args):
+    """The learned surrogate's tensor-core kernels at the training shapes (4
+    members, batch 4096, 60 increments, synthetic features and targets): one
+    bench step = one AdamW step of every member (whole-forward tcgen05 kernel
+    with the BPTT tape, tcgen05 data gradients, split-K weight gradients); then
+    the ensemble prediction of the same batch, whose kernel carries the tensor
+    roofline."""
+    import torch
+
+    from paper_1902_09171_gb300 import build, rcell
+    from paper_1902_09171_gb300 import surrogate as S
+    build.build()
+    rcell.load()
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    B, T, K = 4096, 60, 4
+    rng = np.random.default_rng(0)
+    U = torch.tensor(rng.standard_normal((B, T, 15)), dtype=torch.float32, device="cuda")
+    Y = torch.tensor(rng.standard_normal((B, T, 6)), dtype=torch.float32, device="cuda")
+    s = S.sur_create(K, B, T, 1, stream=st)
+    for _ in range(args.warmup):
+        S.sur_train_step(s, U, Y, 1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        S.sur_train_step(s, U, Y, 1e-3, want_loss=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    P = torch.zeros((K, B, T, 6), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        S.sur_predict(s, U, P)
+    torch.cuda.synchronize()
+    n_pred = 10
+    e0.record(st)
+    for _ in range(n_pred):
+        S.sur_predict(s, U, P)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_pred = e0.elapsed_time(e1) / n_pred
+    err = S.sur_sync(s)
+    S.sur_destroy(s)
+    flop_fwd = 2.0 * B * T * (144 * 256 + 2 * 256 * 256 + 256 * 144) * K
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    peak = float(peaks["bf16_tflops"])
+    achieved = flop_fwd / (ms_pred / 1e3) / 1e12
+    return {"metric": "surrogate training throughput (sequence-increments/s, 4-member ensemble)",
+            "value": B * T * K / (ms / 1e3), "unit": "sequence-increments/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "status": err, "data": "synthetic",
+            "dtype": "bf16 operands, f32 accumulation / master weights",
+            "config": {"workload": "surrogate_train_4x4096x60", "members": K, "batch": B, "increments": T},
+            "train_tflops": 3 * flop_fwd / (ms / 1e3) / 1e12,
+            "predict_ms": ms_pred,
+            "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_forward_fused (prediction)",
+                         "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
+
+
 def run_surrogate_fe(args):
     """The learned surrogate against plain r-cell MD on an FE bar of Kremer-Grest
     r-cells (5000 beads each): S1 data generation through batched r-cells, BF16
@@ -568,7 +627,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics"])
+    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics", "surrogate_train"])
     ap.add_argument("--kg-cells", type=int, default=64)
     ap.add_argument("--pushoff", type=int, default=60)
     ap.add_argument("--paths", type=int, default=1024)
@@ -584,7 +643,8 @@ def main():
     if args.workload != "copper_bar":
         if args.md_steps == MD_STEPS and args.workload == "kg_bar":
             args.md_steps = 1000
-        run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "kg_statics": run_kg_statics}[args.workload]
+        run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "kg_statics": run_kg_statics,
+               "surrogate_train": run_surrogate_train}[args.workload]
         out = run(args)
         print(json.dumps(out))
         return
