@@ -150,6 +150,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one k_force<SC> launch on this workload (128 000
+# atoms, skin 1.5 A), from an ncu capture of the current kernel (--set full,
+# the non-sampling variant): 123.04 MB read + 4.59 MB written.  Mostly the
+# Verlet list, re-read from DRAM every launch.
+K_FORCE_DRAM_BYTES = 127.63e6
+
+
 def fp32_unit_peak_tflops():
     """FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128
     FP32 lanes x 2 FLOP per FMA x 2070 MHz."""
@@ -261,7 +268,7 @@ def run_ours(args):
     t_ns, t_s = prof["force"], prof.get("force_sample", prof["force"])
     achieved = (n_ns * force_ns + n_s * force_s) * n_atoms / ((n_ns * t_ns + n_s * t_s) / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "frac": round(achieved / fp32_peak, 4), "traffic": K_FORCE_DRAM_BYTES if args.skin == 1.5 else None,
                 "kernel": "k_force<SC> (force + Verlet/Langevin (+ virial on sampling steps))",
                 "peak_source": "measured: FFMA probe on this GPU (rcell_fp32_peak), %.2f TFLOP/s; unit-count "
                                "figure 152 SMs x 128 lanes x 2 FLOP x 2070 MHz = %.2f TFLOP/s"
