@@ -378,6 +378,10 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _kg_melt_job(n_chains, chain_len, density, seed, pushoff):
+    return inputs.kg_melt(n_chains, chain_len, density, seed=seed, pushoff_iters=pushoff)
+
+
 def run_kg_bar(args):
     """Uneven Kremer-Grest r-cells (sizes U[5000, 20000] beads in chains of 50, seed 3)
     on a 4x4x4 hex mesh, one FE increment = one bench step (uniaxial tension to 30 %
@@ -390,13 +394,21 @@ def run_kg_bar(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sizes = inputs.uniform_sizes(args.kg_cells, 5000, 20000, 50, 3)
-    cells = []
-    for k, n in enumerate(sizes):
-        x, H, b = inputs.kg_melt(int(n) // 50, 50, 0.85, seed=300 + k, pushoff_iters=args.pushoff)
-        cells.append(dict(H0=H, x0=inputs.to_f32(x), bonds=b))
+    # the seeded melts (NumPy push-off of overlapping beads) in a spawned process pool
+    import multiprocessing as mp
+    jobs = [(int(n) // 50, 50, 0.85, 300 + k, args.pushoff) for k, n in enumerate(sizes)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        melts = pool.starmap(_kg_melt_job, jobs)
+    cells = [dict(H0=H, x0=inputs.to_f32(x), bonds=b) for x, H, b in melts]
+    # melt preparation (as for the surrogate data): displacement-limited soft start,
+    # then equilibration with the production parameters; the timed increments
+    # start from these states
     soft = rcell.params_kg(tau=0.5, kT=1.0, dt=0.002, seed=3, max_step=0.02)
     ctx = rcell.rcell_create(soft, cells, stream=stream)
-    rcell.rcell_run(ctx, 1000, 0)
+    rcell.rcell_run(ctx, 2000, 0)
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("KG soft start: " + rcell.rcell_last_error(ctx))
     eq = []
     for k, c in enumerate(cells):
         x, v, _ = rcell.rcell_get_atoms(ctx, k, len(c["x0"]))
@@ -404,6 +416,10 @@ def run_kg_bar(args):
     rcell.rcell_destroy(ctx)
     ctx = rcell.rcell_create(rcell.params_kg(), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, args.tpa or 1, 1)
+    rcell.rcell_run(ctx, 2000, 0)
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("KG equilibration: " + rcell.rcell_last_error(ctx))
     L = float(np.mean([c["H0"][0, 0] for c in cells]))
     m = int(round(len(cells) ** (1 / 3)))
     X, conn = inputs.hex_mesh(m, m, m, m * L, m * L, m * L)
@@ -413,6 +429,9 @@ def run_kg_bar(args):
     for k in range(args.warmup):
         rcell.fe_step(fe, ctx, 0.3 * (k + 1) / 60, md, md // 2, None)
     torch.cuda.synchronize()
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("KG warm-up increments: " + rcell.rcell_last_error(ctx))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
         ev[k][0].record(stream)
@@ -422,12 +441,15 @@ def run_kg_bar(args):
     st = rcell.rcell_sync(ctx)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     n_atoms = int(sizes.sum())
+    Fe = np.zeros((len(cells), 3, 3))
+    rcell.fe_get_F(fe, Fe)
     out = {"metric": "atom-steps/s batched r-cell MD (Kremer-Grest bar, uneven cells)",
            "value": n_atoms * md * args.steps / (ms / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "status": rcell.STATUS[st], "data": "synthetic",
            "config": {"workload": f"kg_bar_{len(cells)}_cells_5k_20k", "atoms": n_atoms, "md_steps": md},
-           "fe_load_steps_per_s": args.steps / (ms / 1e3)}
+           "fe_load_steps_per_s": args.steps / (ms / 1e3),
+           "element_F_xx_range": [float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max())]}
     rcell.fe_destroy(fe)
     rcell.rcell_destroy(ctx)
     return out
@@ -636,7 +658,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics", "surrogate_train"])
     ap.add_argument("--kg-cells", type=int, default=64)
-    ap.add_argument("--pushoff", type=int, default=60)
+    ap.add_argument("--pushoff", type=int, default=300)
     ap.add_argument("--paths", type=int, default=1024)
     ap.add_argument("--train-steps", type=int, default=2500)
     args = ap.parse_args()
