@@ -587,6 +587,52 @@ def run_surrogate_train(args):
                          "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
 
 
+def run_kg_tensile(args):
+    """The paper's direct periodic-box MD tensile comparison (Sec. 3.2): 32
+    Kremer-Grest cells of 5000 beads at T = 0.1 (below the glass transition),
+    stretched along x at the engineering strain rate 0.01 / tau with lateral
+    contraction (1 + eps)^-1/2, a new deformation every 50 MD steps (dt 0.005),
+    to 15 % strain.  One bench step = one chunk (deformation, 50 MD steps, stress)."""
+    import torch
+
+    from paper_1902_09171_gb300 import build, pipeline, rcell
+    build.build()
+    rcell.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n_cells, rate, dt, chunk = 32, 0.01, 0.005, 50
+    n_chunks = int(round(0.15 / (rate * dt * chunk)))
+    ctx0, cells = pipeline.prepare_kg_batch(n_cells, stream=stream)
+    rcell.rcell_destroy(ctx0)
+    ctx = rcell.rcell_create(rcell.params_kg(kT=0.1, seed=7), cells, stream=stream)
+    rcell.rcell_run(ctx, 2000, 0)  # cool to T = 0.1
+    for _ in range(args.warmup):
+        rcell.rcell_run(ctx, chunk, chunk)
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("KG tensile preparation: " + rcell.rcell_last_error(ctx))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    eps, sig = pipeline.pbc_tensile(ctx, rate, dt, n_chunks, chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = rcell.rcell_sync(ctx)
+    n_atoms = rcell.rcell_info(ctx)[1]
+    sxx = sig[:, :, 0].mean(1)
+    out = {"metric": "atom-steps/s, periodic-box MD tensile test (Kremer-Grest glass, T = 0.1)",
+           "value": n_atoms * chunk * n_chunks / (ms / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
+           "steps": n_chunks, "warmup": args.warmup, "ms_per_step": ms / n_chunks, "higher_is_better": True,
+           "status": rcell.STATUS[st], "data": "synthetic", "dtype": "f32 (pair math) / f64 (stress)",
+           "config": {"workload": f"kg_tensile_{n_cells}x5000", "strain_rate": rate, "md_steps_per_chunk": chunk,
+                      "final_strain": float(eps[-1])},
+           "stress_xx_at_strain": {f"{e:.3f}": round(float(v), 4) for e, v in zip(eps[4::6], sxx[4::6])},
+           "strain_at_max_stress": float(eps[int(np.argmax(sxx))])}
+    rcell.rcell_destroy(ctx)
+    return out
+
+
 def run_surrogate_fe(args):
     """The learned surrogate against plain r-cell MD on an FE bar of Kremer-Grest
     r-cells (5000 beads each): S1 data generation through batched r-cells, BF16
@@ -656,7 +702,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics", "surrogate_train"])
+    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics", "surrogate_train", "kg_tensile"])
     ap.add_argument("--kg-cells", type=int, default=64)
     ap.add_argument("--pushoff", type=int, default=300)
     ap.add_argument("--paths", type=int, default=1024)
@@ -673,7 +719,7 @@ def main():
         if args.md_steps == MD_STEPS and args.workload == "kg_bar":
             args.md_steps = 1000
         run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "kg_statics": run_kg_statics,
-               "surrogate_train": run_surrogate_train}[args.workload]
+               "surrogate_train": run_surrogate_train, "kg_tensile": run_kg_tensile}[args.workload]
         out = run(args)
         print(json.dumps(out))
         return

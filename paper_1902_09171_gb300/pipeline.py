@@ -204,3 +204,27 @@ def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n
     res["max_rel_dev"] = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30))
     res["md_fraction"] = float(sum(res["n_md"]) / (ne * len(lambdas)))
     return res
+
+
+def tensile_F(eps, nu=0.5):
+    """Uniaxial stretch along x with lateral contraction (1 + eps)^-nu."""
+    lam = 1.0 + eps
+    return np.diag([lam, lam ** -nu, lam ** -nu])
+
+
+def pbc_tensile(ctx, rate, dt, n_chunks, chunk_steps, nu=0.5, eps0=0.0):
+    """Direct periodic-box MD tensile test of every r-cell (the comparison run of
+    Sec. 3.2): the box follows a uniaxial engineering strain that grows at `rate`
+    per unit time, applied as a new deformation (QR, remap) every `chunk_steps` MD
+    steps, each chunk averaging the stress over its steps.  Returns the strains
+    and the per-cell FE-frame stresses (n_chunks, n_cells, 6)."""
+    n = rcell.rcell_info(ctx)[0]
+    eps, sig = [], []
+    for k in range(1, n_chunks + 1):
+        e = eps0 + rate * dt * chunk_steps * k
+        rcell.rcell_set_deformation(ctx, np.tile(tensile_F(e, nu), (n, 1, 1)))
+        rcell.rcell_run(ctx, chunk_steps, chunk_steps)
+        s, _, _ = rcell.rcell_stress(ctx)
+        eps.append(e)
+        sig.append(s)
+    return np.array(eps), np.array(sig)
