@@ -103,6 +103,9 @@ def lib():
         L.or_md_run.argtypes = [C.POINTER(Pot), C.POINTER(MD), C.c_int, D, D, D, C.c_int, I, C.c_uint32,
                                 C.POINTER(C.c_uint64), C.c_int, C.c_int, D, D, D]
         L.or_block_stats.argtypes = [C.c_int, D, C.c_int, D, D]
+        L.or_fe_tet_geometry.argtypes = [C.c_int, D, C.c_int, I, C.c_double, D, D, D]
+        L.or_fe_tet_F.argtypes = [C.c_int, I, D, D, D]
+        L.or_fe_tet_update.argtypes = [C.c_int, C.c_int, I, D, D, D, I, D, C.c_double, C.c_double, D, D, D]
         L.or_pk1_pairs.argtypes = [C.POINTER(Pot), C.c_int, C.c_int, D, D, D, C.c_int, I, D]
         L.or_fire_minimize.argtypes = [C.POINTER(Pot), C.c_int, C.c_double, C.c_int, D, D, C.c_int, I, C.c_double,
                                        C.c_double, C.c_double, C.c_double, C.c_int, I]
@@ -339,4 +342,41 @@ class FEMesh:
         lib().or_fe_update(self.nn, _dp(self.X), self.ne, _ip(self.conn), _dp(self.gradN), _dp(self.V0),
                            _dp(self.mass), _ip(self.bc_mask), _dp(P), self.hg, self.dt, self.damping, _dp(self.d),
                            _dp(self.v), _dp(fint))
+        return fint
+
+
+class FETetMesh:
+    """Explicit 4-node tetrahedron FE driver state (FP64), the same step order as FEMesh."""
+
+    def __init__(self, X, conn, bc_mask, bc_val, rho0, dt, damping):
+        self.X = _f64(X, (-1, 3))
+        self.conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 4)
+        self.nn, self.ne = self.X.shape[0], self.conn.shape[0]
+        self.bc_mask = np.ascontiguousarray(bc_mask, dtype=np.int32).reshape(-1, 3)
+        self.bc_val = _f64(bc_val, (-1, 3))
+        self.dt, self.damping = dt, damping
+        self.gradN = np.zeros((self.ne, 4, 3))
+        self.V0 = np.zeros(self.ne)
+        self.mass = np.zeros(self.nn)
+        e = lib().or_fe_tet_geometry(self.nn, _dp(self.X), self.ne, _ip(self.conn), rho0, _dp(self.gradN),
+                                     _dp(self.V0), _dp(self.mass))
+        if e:
+            raise OracleError(e, "fe tet geometry")
+        self.d = np.zeros((self.nn, 3))
+        self.v = np.zeros((self.nn, 3))
+
+    def apply_bc(self, lam):
+        lib().or_fe_apply_bc(self.nn, _ip(self.bc_mask), _dp(self.bc_val), lam, _dp(self.d))
+
+    def F(self):
+        F = np.zeros((self.ne, 3, 3))
+        lib().or_fe_tet_F(self.ne, _ip(self.conn), _dp(self.gradN), _dp(self.d), _dp(F))
+        return F
+
+    def update(self, P):
+        P = _f64(P, (self.ne, 3, 3))
+        fint = np.zeros((self.nn, 3))
+        lib().or_fe_tet_update(self.nn, self.ne, _ip(self.conn), _dp(self.gradN), _dp(self.V0), _dp(self.mass),
+                               _ip(self.bc_mask), _dp(P), self.dt, self.damping, _dp(self.d), _dp(self.v),
+                               _dp(fint))
         return fint

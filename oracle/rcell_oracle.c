@@ -816,6 +816,83 @@ void or_fe_update(int nn, const double *X, int ne, const int *conn, const double
 }
 
 /* ------------------------------------------------------------------------ */
+/* 4-node tetrahedra, the paper's element (C3D4, Sec. 2.2): linear shape     */
+/* functions N = (1 - xi - eta - zeta, xi, eta, zeta), so grad N and F are    */
+/* constant in the element; one quadrature point (one r-cell), no hourglass  */
+/* modes.  Lumped mass rho0 V / 4 per node; the same explicit update.        */
+/* ------------------------------------------------------------------------ */
+static const int TET_DN[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+/* grad_X N_a (4x3) and the volume det J / 6, J_{i alpha} = sum_a X_{a i} dN_a/dxi_alpha */
+int or_tet4_geometry(const double *X, double *gradN, double *V0) {
+    double J[9] = {0};
+    for (int a = 0; a < 4; a++)
+        for (int i = 0; i < 3; i++)
+            for (int al = 0; al < 3; al++) J[3 * i + al] += X[3 * a + i] * TET_DN[a][al];
+    double Ji[9];
+    double det = m3_inv(J, Ji);
+    if (!(det > 0.0)) return OR_EDEGEN;
+    for (int a = 0; a < 4; a++)
+        for (int k = 0; k < 3; k++) {
+            double s = 0.0;
+            for (int al = 0; al < 3; al++) s += Ji[3 * al + k] * TET_DN[a][al];
+            gradN[3 * a + k] = s;
+        }
+    *V0 = det / 6.0;
+    return OR_OK;
+}
+
+int or_fe_tet_geometry(int nn, const double *X, int ne, const int *conn, double rho0, double *gradN, double *V0,
+                       double *mass) {
+    for (int a = 0; a < nn; a++) mass[a] = 0.0;
+    for (int e = 0; e < ne; e++) {
+        double Xe[12];
+        for (int a = 0; a < 4; a++)
+            for (int k = 0; k < 3; k++) Xe[3 * a + k] = X[3 * conn[4 * e + a] + k];
+        int err = or_tet4_geometry(Xe, gradN + 12 * e, V0 + e);
+        if (err) return err;
+        for (int a = 0; a < 4; a++) mass[conn[4 * e + a]] += rho0 * V0[e] / 4.0;
+    }
+    return OR_OK;
+}
+
+/* F = I + sum_a d_a (x) grad_X N_a per element (ne x 9) */
+void or_fe_tet_F(int ne, const int *conn, const double *gradN, const double *d, double *F) {
+    for (int e = 0; e < ne; e++)
+        for (int i = 0; i < 3; i++)
+            for (int J = 0; J < 3; J++) {
+                double s = (i == J) ? 1.0 : 0.0;
+                for (int a = 0; a < 4; a++) s += d[3 * conn[4 * e + a] + i] * gradN[12 * e + 3 * a + J];
+                F[9 * e + 3 * i + J] = s;
+            }
+}
+
+/* One explicit step (as or_fe_update) with f_int,a = V0 P grad_X N_a (Eq. f) */
+void or_fe_tet_update(int nn, int ne, const int *conn, const double *gradN, const double *V0, const double *mass,
+                      const int *bc_mask, const double *P, double dt, double damping, double *d, double *vel,
+                      double *fint_out) {
+    double *fint = (double *)calloc((size_t)3 * nn, sizeof(double));
+    for (int e = 0; e < ne; e++)
+        for (int a = 0; a < 4; a++)
+            for (int i = 0; i < 3; i++) {
+                double s = 0.0;
+                for (int J = 0; J < 3; J++) s += P[9 * e + 3 * i + J] * gradN[12 * e + 3 * a + J];
+                fint[3 * conn[4 * e + a] + i] += V0[e] * s;
+            }
+    double c0 = 1.0 - 0.5 * damping * dt, c1 = 1.0 + 0.5 * damping * dt;
+    for (int a = 0; a < nn; a++)
+        for (int k = 0; k < 3; k++) {
+            int q = 3 * a + k;
+            if (bc_mask[q]) { vel[q] = 0.0; continue; }
+            double acc = -fint[q] / mass[a];
+            vel[q] = (c0 * vel[q] + dt * acc) / c1;
+            d[q] += dt * vel[q];
+        }
+    if (fint_out) memcpy(fint_out, fint, sizeof(double) * 3 * (size_t)nn);
+    free(fint);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Molecular statics of an r-cell (Sec. 2.1, Eqs. CGPR1-CGPR3 and PK1).      */
 /* ------------------------------------------------------------------------ */
 

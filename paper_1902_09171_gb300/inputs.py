@@ -76,6 +76,24 @@ def hex_mesh(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float):
     return np.ascontiguousarray(X), np.asarray(conn, dtype=np.int32)
 
 
+def tet_mesh(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float):
+    """The structured hex mesh of hex_mesh split into 4-node tetrahedra: six per
+    hexahedron around its (-,-,-)-(+,+,+) diagonal, the same diagonal direction
+    in every hexahedron so that neighbouring faces match; every tetrahedron has
+    positive orientation.  Returns X (nn, 3) and conn (6 nx ny nz, 4)."""
+    X, hexes = hex_mesh(nx, ny, nz, Lx, Ly, Lz)
+    split = [(0, 1, 2, 6), (0, 2, 3, 6), (0, 3, 7, 6), (0, 7, 4, 6), (0, 4, 5, 6), (0, 5, 1, 6)]
+    conn = []
+    for h in hexes:
+        for t in split:
+            q = [int(h[a]) for a in t]
+            e1, e2, e3 = X[q[1]] - X[q[0]], X[q[2]] - X[q[0]], X[q[3]] - X[q[0]]
+            if np.dot(np.cross(e1, e2), e3) < 0:
+                q[1], q[2] = q[2], q[1]
+            conn.append(q)
+    return X, np.asarray(conn, dtype=np.int32)
+
+
 def uniaxial_bc(X: np.ndarray, L: float, all_nodes: bool = False):
     """Boundary conditions for uniaxial extension along x (load factor = engineering strain).
 
