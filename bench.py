@@ -58,9 +58,12 @@ def make_cells(n_cells, seed0=1000):
     return [dict(H0=H, x0=x, v0=inputs.to_f32(inputs.maxwell(len(x), MASS, KT, 0, seed0 + c))) for c in range(n_cells)]
 
 
-def mesh():
+def mesh(element="hex8"):
+    """The bar's mesh: 8 x 2 x 2 hexahedra, or the same box in 6 tetrahedra per
+    hexahedron (the paper's C3D4 element)."""
     L = NC * A_LAT
-    X, conn = inputs.hex_mesh(*MESH, MESH[0] * L, MESH[1] * L, MESH[2] * L)
+    gen = inputs.tet_mesh if element == "tet4" else inputs.hex_mesh
+    X, conn = gen(*MESH, MESH[0] * L, MESH[1] * L, MESH[2] * L)
     mask, val = inputs.uniaxial_bc(X, MESH[0] * L)
     return X, conn, mask, val
 
@@ -189,16 +192,19 @@ def run_ours(args):
     rcell.load()
     stream = torch.cuda.Stream()  # a dedicated stream: library kernels, flushes and events all on it
     torch.cuda.set_stream(stream)
-    n_total = MESH[0] * MESH[1] * MESH[2]
+    X, conn, mask, val = mesh(args.element)
+    n_total = len(conn)  # one r-cell per element
     # weak scaling: each rank runs a full copper bar (its own independent cells)
     cells = make_cells(n_total, seed0=1000 + rank * n_total)
-    X, conn, mask, val = mesh()
     prm = rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=12345 + rank, skin=args.skin)
     ctx = rcell.rcell_create(prm, cells, stream=stream)
     if args.tpa:
         rcell.rcell_set_tuning(ctx, args.tpa, -1)
     rho0, dt_fe, damp_fe, hg_fe = fe_params()
-    fe = rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=stream)
+    if args.element == "tet4":  # tetrahedra: shorter altitudes, half the step; no hourglass control
+        fe = rcell.fe_create_tet4(X, conn, mask, val, rho0, 0.5 * dt_fe, damp_fe, stream=stream)
+    else:
+        fe = rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=stream)
     n_atoms = sum(len(c["x0"]) for c in cells)
     md = args.md_steps
     navg = min(N_AVG, md // 2)
@@ -268,7 +274,7 @@ def run_ours(args):
     t_ns, t_s = prof["force"], prof.get("force_sample", prof["force"])
     achieved = (n_ns * force_ns + n_s * force_s) * n_atoms / ((n_ns * t_ns + n_s * t_s) / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": K_FORCE_DRAM_BYTES if args.skin == 1.5 else None,
+                "frac": round(achieved / fp32_peak, 4), "traffic": K_FORCE_DRAM_BYTES if (args.skin == 1.5 and args.element == "hex8") else None,
                 "kernel": "k_force<SC> (force + Verlet/Langevin (+ virial on sampling steps))",
                 "peak_source": "measured: FFMA probe on this GPU (rcell_fp32_peak), %.2f TFLOP/s; unit-count "
                                "figure 152 SMs x 128 lanes x 2 FLOP x 2070 MHz = %.2f TFLOP/s"
@@ -279,11 +285,12 @@ def run_ours(args):
     out = None
     if rank == 0:
         out = {
-            "metric": "atom-steps/s batched r-cell MD (copper bar, Sutton-Chen EAM, 32 x 4000 atoms)",
+            "metric": "atom-steps/s batched r-cell MD (copper bar, Sutton-Chen EAM, %d x 4000 atoms)" % n_total,
             "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (pair math) / f64 (QR, remap, virial accumulation, FE)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": n_total * world, "atoms_per_cell": NC ** 3 * 4,
+            "config": {"workload": WORKLOAD if args.element == "hex8" else "copper_bar_sc_eam_tet4_%dx4000" % n_total,
+                       "element": args.element, "cells": n_total * world, "atoms_per_cell": NC ** 3 * 4,
                        "md_steps_per_increment": md, "n_avg": navg, "mesh": list(MESH), "l2": "flushed (256 MB write)",
                        "parallelism": f"{world} independent cell batches" if world > 1 else "single GPU"},
             "fe_load_steps_per_s": args.steps / (ms / 1e3),
@@ -698,6 +705,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--md-steps", type=int, default=MD_STEPS)
     ap.add_argument("--skin", type=float, default=1.5)
+    ap.add_argument("--element", default="hex8", choices=["hex8", "tet4"],
+                    help="FE element of the copper bar: 8-node hexahedra (32 r-cells) or 4-node tetrahedra (192)")
     ap.add_argument("--tpa", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -302,6 +302,18 @@ void rcell_destroy(rcell_ctx *ctx);
 int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mask, const double *bc_val,
               double rho0, double dt, double damping, double hg_coef, void *stream, fe_ctx **out);
 
+/* The same explicit FE with 4-node tetrahedra, the element the paper uses
+ * (C3D4, Sec. 2.2): shape functions N = (1 - xi - eta - zeta, xi, eta, zeta)
+ * on the reference tetrahedron, so grad N and F = I + sum_a d_a (x) grad N_a
+ * are constant in the element (one quadrature point, one r-cell per element)
+ * and there are no hourglass modes (no stabilisation).  Lumped mass
+ * rho0 V / 4 per node.  tet: ne x 4 node ids (host) with positive orientation
+ * ((X1 - X0) x (X2 - X0)) . (X3 - X0) > 0; other arguments as fe_create.
+ * Every other fe_* call works on the returned context unchanged.  RC_EINVAL for
+ * bad ids or an element of zero or negative volume. */
+int fe_create_tet4(const double *X, int nn, const int *tet, int ne, const int *bc_mask, const double *bc_val,
+                   double rho0, double dt, double damping, void *stream, fe_ctx **out);
+
 /* Set the prescribed DOFs to lambda * bc_val.  Asynchronous. */
 int fe_apply_bc(fe_ctx *fe, double lambda);
 

@@ -1,7 +1,9 @@
-// Explicit finite elements in FP64 (Sec. 2.2, Eq. f): 8-node hexahedra, one
-// centroid quadrature point per element (one r-cell each), lumped mass,
-// Flanagan-Belytschko stiffness hourglass control, damped central-difference
-// update.  One thread per element / per DOF; nodal sums by FP64 atomics.
+// Explicit finite elements in FP64 (Sec. 2.2, Eq. f): 8-node hexahedra (one
+// centroid quadrature point, Flanagan-Belytschko stiffness hourglass control)
+// or 4-node tetrahedra (the paper's C3D4: linear, constant gradients, no
+// hourglass modes); one quadrature point and one r-cell per element, lumped
+// mass, damped central-difference update.  One thread per element / per DOF;
+// nodal sums by FP64 atomics.  NPE = nodes per element (8 or 4).
 #include "rc_internal.cuh"
 
 namespace {
@@ -10,16 +12,26 @@ namespace {
 __constant__ signed char c_nat[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
                                         {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
 
+// tetrahedron: N = (1 - xi - eta - zeta, xi, eta, zeta), dN_a/dxi_alpha
+__constant__ signed char c_tet[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+// dN_a/dxi_alpha at the quadrature point
+template <int NPE>
+__device__ __forceinline__ double dshape(int a, int al) {
+    return NPE == 8 ? 0.125 * c_nat[a][al] : (double)c_tet[a][al];
+}
+
+template <int NPE>
 __global__ void k_geometry(const double *__restrict__ X, const int *__restrict__ conn, int ne, double rho0,
                            double *gradN, double *V0, double *mass, int *err) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
-    // J_{i alpha} = sum_a X_{a i} dN_a/dxi_alpha, dN_a/dxi_alpha = nat_a,alpha / 8 at the centroid
+    // J_{i alpha} = sum_a X_{a i} dN_a/dxi_alpha
     double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int a = 0; a < 8; a++) {
-        const double *Xa = X + 3 * conn[8 * e + a];
+    for (int a = 0; a < NPE; a++) {
+        const double *Xa = X + 3 * conn[NPE * e + a];
         for (int i = 0; i < 3; i++)
-            for (int al = 0; al < 3; al++) J[3 * i + al] += Xa[i] * 0.125 * c_nat[a][al];
+            for (int al = 0; al < 3; al++) J[3 * i + al] += Xa[i] * dshape<NPE>(a, al);
     }
     const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
                        J[2] * (J[3] * J[7] - J[4] * J[6]);
@@ -38,15 +50,15 @@ __global__ void k_geometry(const double *__restrict__ X, const int *__restrict__
     Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
     Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
     // grad_X N_a = J^{-T} dN_a/dxi
-    for (int a = 0; a < 8; a++)
+    for (int a = 0; a < NPE; a++)
         for (int k = 0; k < 3; k++) {
             double s = 0.0;
-            for (int al = 0; al < 3; al++) s += Ji[3 * al + k] * 0.125 * c_nat[a][al];
-            gradN[24 * e + 3 * a + k] = s;
+            for (int al = 0; al < 3; al++) s += Ji[3 * al + k] * dshape<NPE>(a, al);
+            gradN[3 * NPE * e + 3 * a + k] = s;
         }
-    const double V = 8.0 * det;
+    const double V = NPE == 8 ? 8.0 * det : det / 6.0;  // reference volumes 8 and 1/6
     V0[e] = V;
-    for (int a = 0; a < 8; a++) atomicAdd(&mass[conn[8 * e + a]], rho0 * V / 8.0);
+    for (int a = 0; a < NPE; a++) atomicAdd(&mass[conn[NPE * e + a]], rho0 * V / NPE);
 }
 
 __global__ void k_apply_bc(const int *__restrict__ mask, const double *__restrict__ val, double lambda, double *d,
@@ -55,14 +67,15 @@ __global__ void k_apply_bc(const int *__restrict__ mask, const double *__restric
     if (q < n3 && mask[q]) d[q] = lambda * val[q];
 }
 
+template <int NPE>
 __global__ void k_F(const int *__restrict__ conn, const double *__restrict__ gradN, const double *__restrict__ d,
                     double *F, int ne) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     double G[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-    for (int a = 0; a < 8; a++) {
-        const double *da = d + 3 * conn[8 * e + a];
-        const double *ga = gradN + 24 * e + 3 * a;
+    for (int a = 0; a < NPE; a++) {
+        const double *da = d + 3 * conn[NPE * e + a];
+        const double *ga = gradN + 3 * NPE * e + 3 * a;
         for (int i = 0; i < 3; i++)
             for (int J = 0; J < 3; J++) G[3 * i + J] += da[i] * ga[J];
     }
@@ -72,18 +85,19 @@ __global__ void k_F(const int *__restrict__ conn, const double *__restrict__ gra
 // f_int,a = V0 P grad N_a + kappa sum_alpha gamma_{alpha a} q_alpha, kappa = hg V0^{1/3},
 // gamma_{alpha a} = (h_{alpha a} - (sum_b h_{alpha b} X_b) . grad N_a) / 8,
 // h = (eta zeta, zeta xi, xi eta, xi eta zeta) at the nodes, q_alpha = sum_b gamma_{alpha b} d_b.
+template <int NPE>
 __global__ void k_fint(const double *__restrict__ X, const int *__restrict__ conn, const double *__restrict__ gradN,
                        const double *__restrict__ V0, const double *__restrict__ P, const double *__restrict__ d,
                        double hg, double *fint, int ne) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
-    const double *g = gradN + 24 * e, *Pe = P + 9 * e;
+    const double *g = gradN + 3 * NPE * e, *Pe = P + 9 * e;
     const double V = V0[e];
-    double fe[24];
-    for (int a = 0; a < 8; a++)
+    double fe[3 * NPE];
+    for (int a = 0; a < NPE; a++)
         for (int i = 0; i < 3; i++)
             fe[3 * a + i] = V * (Pe[3 * i] * g[3 * a] + Pe[3 * i + 1] * g[3 * a + 1] + Pe[3 * i + 2] * g[3 * a + 2]);
-    if (hg != 0.0) {
+    if (NPE == 8 && hg != 0.0) {
         const double kappa = hg * cbrt(V);
         for (int al = 0; al < 4; al++) {
             double h[8], hX[3] = {0, 0, 0};
@@ -107,8 +121,8 @@ __global__ void k_fint(const double *__restrict__ X, const int *__restrict__ con
                 for (int i = 0; i < 3; i++) fe[3 * a + i] += kappa * gam[a] * q[i];
         }
     }
-    for (int a = 0; a < 8; a++)
-        for (int i = 0; i < 3; i++) atomicAdd(&fint[3 * conn[8 * e + a] + i], fe[3 * a + i]);
+    for (int a = 0; a < NPE; a++)
+        for (int i = 0; i < 3; i++) atomicAdd(&fint[3 * conn[NPE * e + a] + i], fe[3 * a + i]);
 }
 
 __global__ void k_update(const int *__restrict__ mask, const double *__restrict__ mass, const double *__restrict__ fint,
@@ -192,21 +206,24 @@ void fe_launch_copy_F(const double *F, double *F_prev, int ne, cudaStream_t s) {
     k_copy_F<<<(9 * ne + 255) / 256, 256, 0, s>>>(F, F_prev, 9 * ne);
 }
 
-void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
+void fe_launch_geometry(int npe, const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
                         double *mass, int *err, cudaStream_t s) {
-    k_geometry<<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
+    if (npe == 4) k_geometry<4><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
+    else k_geometry<8><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
 }
 void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
                         cudaStream_t s) {
     (void)v;
     k_apply_bc<<<(n3 + 255) / 256, 256, 0, s>>>(mask, val, lambda, d, n3);
 }
-void fe_launch_F(const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s) {
-    k_F<<<(ne + 127) / 128, 128, 0, s>>>(conn, gradN, d, F, ne);
+void fe_launch_F(int npe, const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s) {
+    if (npe == 4) k_F<4><<<(ne + 127) / 128, 128, 0, s>>>(conn, gradN, d, F, ne);
+    else k_F<8><<<(ne + 127) / 128, 128, 0, s>>>(conn, gradN, d, F, ne);
 }
-void fe_launch_fint(const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
+void fe_launch_fint(int npe, const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
                     const double *d, double hg, double *fint, int ne, cudaStream_t s) {
-    k_fint<<<(ne + 127) / 128, 128, 0, s>>>(X, conn, gradN, V0, P, d, hg, fint, ne);
+    if (npe == 4) k_fint<4><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, gradN, V0, P, d, hg, fint, ne);
+    else k_fint<8><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, gradN, V0, P, d, hg, fint, ne);
 }
 void fe_launch_update(const int *mask, const double *mass, const double *fint, double dt, double damping, double *d,
                       double *v, int n3, cudaStream_t s) {

@@ -198,12 +198,12 @@ void rc_launch_static_finish(const double *acc, const double *H0, const double *
 void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s);
 
 // finite elements (k_fe.cu)
-void fe_launch_geometry(const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
+void fe_launch_geometry(int npe, const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
                         double *mass, int *err, cudaStream_t s);
 void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
                         cudaStream_t s);
-void fe_launch_F(const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s);
-void fe_launch_fint(const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
+void fe_launch_F(int npe, const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s);
+void fe_launch_fint(int npe, const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
                     const double *d, double hg, double *fint, int ne, cudaStream_t s);
 void fe_launch_update(const int *mask, const double *mass, const double *fint, double dt, double damping,
                       double *d, double *v, int n3, cudaStream_t s);

@@ -65,6 +65,7 @@ struct fe_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nn = 0, ne = 0;
+    int npe = 8;  // nodes per element: 8 (hexahedra) or 4 (tetrahedra)
     double rho0 = 0, dt = 0, damping = 0, hg = 0;
     std::vector<void *> allocs;
     double *d_X = nullptr, *d_val = nullptr, *d_gradN = nullptr, *d_V0 = nullptr, *d_mass = nullptr;
@@ -847,13 +848,19 @@ void rcell_destroy(rcell_ctx *c) {
         if (e_ != cudaSuccess) { (fe)->err = cudaGetErrorString(e_); return RC_ECUDA; }   \
     } while (0)
 
-int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mask, const double *bc_val, double rho0,
-              double dt, double damping, double hg_coef, void *stream, fe_ctx **out) {
+}  // extern "C"
+
+namespace {
+
+int fe_create_npe(int npe, const double *X, int nn, const int *conn, int ne, const int *bc_mask, const double *bc_val,
+                  double rho0, double dt, double damping, double hg_coef, void *stream, fe_ctx **out) {
+    const int *hex = conn;
     if (!X || !hex || !bc_mask || !bc_val || !out || nn <= 0 || ne <= 0 || !(rho0 > 0) || !(dt > 0)) return RC_EINVAL;
-    for (int k = 0; k < 8 * ne; k++)
+    for (int k = 0; k < npe * ne; k++)
         if (hex[k] < 0 || hex[k] >= nn) return RC_EINVAL;
     fe_ctx *fe = new fe_ctx();
     *out = nullptr;
+    fe->npe = npe;
     fe->nn = nn;
     fe->ne = ne;
     fe->rho0 = rho0;
@@ -872,8 +879,8 @@ int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mas
     CKF(fe, dalloc(L, &fe->d_fint, n3));
     CKF(fe, dalloc(L, &fe->d_mass, nn));
     CKF(fe, dalloc(L, &fe->d_mask, n3));
-    CKF(fe, dalloc(L, &fe->d_conn, 8 * (size_t)ne));
-    CKF(fe, dalloc(L, &fe->d_gradN, 24 * (size_t)ne));
+    CKF(fe, dalloc(L, &fe->d_conn, (size_t)npe * ne));
+    CKF(fe, dalloc(L, &fe->d_gradN, 3 * (size_t)npe * ne));
     CKF(fe, dalloc(L, &fe->d_V0, ne));
     CKF(fe, dalloc(L, &fe->d_F, 9 * (size_t)ne));
     CKF(fe, dalloc(L, &fe->d_P, 9 * (size_t)ne));
@@ -881,8 +888,8 @@ int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mas
     CKF(fe, cudaMemcpy(fe->d_X, X, sizeof(double) * n3, cudaMemcpyHostToDevice));
     CKF(fe, cudaMemcpy(fe->d_val, bc_val, sizeof(double) * n3, cudaMemcpyHostToDevice));
     CKF(fe, cudaMemcpy(fe->d_mask, bc_mask, sizeof(int) * n3, cudaMemcpyHostToDevice));
-    CKF(fe, cudaMemcpy(fe->d_conn, hex, sizeof(int) * 8 * ne, cudaMemcpyHostToDevice));
-    fe_launch_geometry(fe->d_X, fe->d_conn, ne, rho0, fe->d_gradN, fe->d_V0, fe->d_mass, fe->d_err, fe->stream);
+    CKF(fe, cudaMemcpy(fe->d_conn, hex, sizeof(int) * npe * ne, cudaMemcpyHostToDevice));
+    fe_launch_geometry(npe, fe->d_X, fe->d_conn, ne, rho0, fe->d_gradN, fe->d_V0, fe->d_mass, fe->d_err, fe->stream);
     CKF(fe, cudaGetLastError());
     int err = 0;
     CKF(fe, cudaStreamSynchronize(fe->stream));
@@ -890,6 +897,20 @@ int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mas
     if (err) { fe_destroy(fe); return RC_EINVAL; }
     *out = fe;
     return RC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mask, const double *bc_val, double rho0,
+              double dt, double damping, double hg_coef, void *stream, fe_ctx **out) {
+    return fe_create_npe(8, X, nn, hex, ne, bc_mask, bc_val, rho0, dt, damping, hg_coef, stream, out);
+}
+
+int fe_create_tet4(const double *X, int nn, const int *tet, int ne, const int *bc_mask, const double *bc_val,
+                   double rho0, double dt, double damping, void *stream, fe_ctx **out) {
+    return fe_create_npe(4, X, nn, tet, ne, bc_mask, bc_val, rho0, dt, damping, 0.0, stream, out);
 }
 
 int fe_apply_bc(fe_ctx *fe, double lambda) {
@@ -901,7 +922,7 @@ int fe_apply_bc(fe_ctx *fe, double lambda) {
 
 int fe_get_F(fe_ctx *fe, double *F, int where) {
     if (!fe || !F) return RC_EINVAL;
-    fe_launch_F(fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, fe->ne, fe->stream);
+    fe_launch_F(fe->npe, fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, fe->ne, fe->stream);
     CKF(fe, cudaGetLastError());
     CKF(fe, cudaMemcpyAsync(F, fe->d_F, sizeof(double) * 9 * fe->ne,
                             where == RC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, fe->stream));
@@ -917,7 +938,8 @@ int fe_update(fe_ctx *fe, const double *P, int where) {
         dP = fe->d_P;
     }
     CKF(fe, cudaMemsetAsync(fe->d_fint, 0, sizeof(double) * 3 * fe->nn, fe->stream));
-    fe_launch_fint(fe->d_X, fe->d_conn, fe->d_gradN, fe->d_V0, dP, fe->d_d, fe->hg, fe->d_fint, fe->ne, fe->stream);
+    fe_launch_fint(fe->npe, fe->d_X, fe->d_conn, fe->d_gradN, fe->d_V0, dP, fe->d_d, fe->hg, fe->d_fint, fe->ne,
+                   fe->stream);
     fe_launch_update(fe->d_mask, fe->d_mass, fe->d_fint, fe->dt, fe->damping, fe->d_d, fe->d_v, 3 * fe->nn,
                      fe->stream);
     CKF(fe, cudaGetLastError());
@@ -929,7 +951,7 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
     if (rc->n_cells != fe->ne) { fe->err = "one r-cell per element required"; return RC_EINVAL; }
     int e;
     fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, fe->stream);
-    fe_launch_F(fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, fe->ne, fe->stream);
+    fe_launch_F(fe->npe, fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, fe->ne, fe->stream);
     CKF(fe, cudaGetLastError());
     if (fe->stream != rc->stream) {
         CKF(fe, cudaEventRecord(fe->ev, fe->stream));
@@ -974,7 +996,7 @@ int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, in
     int e;
     // 1. boundary conditions and element F
     fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, st);
-    fe_launch_F(fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, ne, st);
+    fe_launch_F(fe->npe, fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, ne, st);
     // 2. surrogate for every point (keeps every recurrent state current)
     if ((e = sur_features(F_prev, fe->d_F, ne, fe->d_u, st)) != RC_OK) return e;
     if ((e = sur_step(sur, fe->d_u, ne, h_state, s_floor, fe->d_smean, fe->d_spread)) != RC_OK) return e;

@@ -48,7 +48,7 @@ _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
            "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_minimize", "rcell_stress_static", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
-           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
+           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_create_tet4", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
 
@@ -91,6 +91,8 @@ def load(path: str | None = None):
         "rcell_destroy": ([vp], None),
         "fe_create": ([vp, C.c_int, vp, C.c_int, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp,
                        C.POINTER(vp)], C.c_int),
+        "fe_create_tet4": ([vp, C.c_int, vp, C.c_int, vp, vp, C.c_double, C.c_double, C.c_double, vp,
+                            C.POINTER(vp)], C.c_int),
         "fe_apply_bc": ([vp, C.c_double], C.c_int),
         "fe_get_F": ([vp, vp, C.c_int], C.c_int),
         "fe_update": ([vp, vp, C.c_int], C.c_int),
@@ -360,6 +362,19 @@ def fe_create(X, hex_conn, bc_mask, bc_val, rho0, dt, damping, hg_coef, stream=N
     _check(load().fe_create(C.c_void_p(X.ctypes.data), X.shape[0], C.c_void_p(hx.ctypes.data), hx.shape[0],
                             C.c_void_p(m.ctypes.data), C.c_void_p(v.ctypes.data), rho0, dt, damping, hg_coef,
                             _stream_ptr(stream), C.byref(out)), None, "fe_create")
+    return out
+
+
+def fe_create_tet4(X, tet_conn, bc_mask, bc_val, rho0, dt, damping, stream=None):
+    """Explicit FE on 4-node tetrahedra (positively oriented); the other fe_* calls are shared."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    tt = np.ascontiguousarray(tet_conn, dtype=np.int32)
+    m = np.ascontiguousarray(bc_mask, dtype=np.int32)
+    v = np.ascontiguousarray(bc_val, dtype=np.float64)
+    out = C.c_void_p()
+    _check(load().fe_create_tet4(C.c_void_p(X.ctypes.data), X.shape[0], C.c_void_p(tt.ctypes.data), tt.shape[0],
+                                 C.c_void_p(m.ctypes.data), C.c_void_p(v.ctypes.data), rho0, dt, damping,
+                                 _stream_ptr(stream), C.byref(out)), None, "fe_create_tet4")
     return out
 
 
