@@ -25,6 +25,7 @@ __global__ void k_fire_init(FireState s, const int *status, const int *active, i
     s.alpha[c] = FIRE_ALPHA0;
     s.npos[c] = 0;
     s.done[c] = (status[c] != 0 || !active[c]) ? 1 : 0;
+    s.moving[c] = 1 - s.done[c];
     s.iters[c] = -1;
     s.it[c] = 0;
     s.mixa[c] = 1.0f;
@@ -88,6 +89,7 @@ __global__ void k_fire_control(FireState s, int n_cells, float f_tol2, float dt_
     s.acc[4 * c] = s.acc[4 * c + 1] = s.acc[4 * c + 2] = 0.0;
     if (f2max < f_tol2) {
         s.done[c] = 1;
+        s.moving[c] = 0;  // the force kernels skip the cell from now on
         s.iters[c] = s.it[c];
         return;
     }

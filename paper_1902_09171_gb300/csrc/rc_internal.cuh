@@ -164,6 +164,7 @@ struct FireState {
     unsigned *fmax2;  // max |f_i|^2 as float bits
     float *dt, *alpha, *mixa, *mixb;
     int *npos, *done, *iters, *it, *zero;
+    int *moving;  // per cell: 1 while the cell minimises (stands in for the activity mask meanwhile)
 };
 
 // host-side launchers (defined in the kernel translation units)

@@ -54,6 +54,8 @@ struct rcell_ctx {
     // molecular statics (allocated on first use)
     FireState fire{};
     int *d_fire_left = nullptr;
+    cudaGraphExec_t fire_graph = nullptr;  // one captured batch of FIRE iterations
+    double fire_key[5] = {0, 0, 0, 0, 0};   // f_tol, dt_max, dmax, tpa, cur it was captured with
     float *d_mcell = nullptr;
     double *d_pk_acc = nullptr;
     std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
@@ -106,6 +108,8 @@ void free_graphs(rcell_ctx *c) {
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     c->graph_launches.clear();
+    if (c->fire_graph) cudaGraphExecDestroy(c->fire_graph);
+    c->fire_graph = nullptr;
 }
 
 int first_status(rcell_ctx *c) {
@@ -629,26 +633,55 @@ int rcell_minimize(rcell_ctx *c, int max_iter, double f_tol, double dt0, double 
         CKC(c, dalloc(L, &f.iters, nc));
         CKC(c, dalloc(L, &f.it, nc));
         CKC(c, dalloc(L, &f.zero, nc));
+        CKC(c, dalloc(L, &f.moving, nc));
         CKC(c, dalloc(L, &c->d_fire_left, 1));
     }
     rc_launch_fire_init(c->fire, c->ka.status, c->ka.active, nc, (float)dt0, c->stream);
     rc_launch_fire_zero_v(c->ka, c->fire, c->n_tiles, 0, c->stream);
+    {
+    // while minimising, the kernels see the per-cell "still moving" flags as the
+    // activity mask, so converged cells cost no more force evaluations; the
+    // caller's mask is back in place on every way out of this block
+    struct MaskSwap {
+        rcell_ctx *c;
+        const int *saved;
+        ~MaskSwap() { c->ka.active = saved; }
+    } swap{c, c->ka.active};
+    c->ka.active = c->fire.moving;
     // iterations in batches between convergence checks: forces (MODE_EVAL, after the
     // list and density kernels), then the FIRE power / control / move kernels
     const int batch = 32;
-    for (int it0 = 0; it0 < max_iter; it0 += batch) {
-        CKC(c, cudaMemsetAsync(c->d_fire_left, 0, sizeof(int), c->stream));
-        const int nb = std::min(batch, max_iter - it0);
+    auto enqueue_batch = [&](int nb) {
+        cudaMemsetAsync(c->d_fire_left, 0, sizeof(int), c->stream);
         for (int k = 0; k < nb; k++) {  // the last iteration of the batch counts the cells still moving
             enqueue_step(c, MODE_EVAL, -1, 0);
             rc_launch_fire_iteration(c->kp, c->ka, c->cur, c->fire, c->n_tiles, nc, (float)f_tol, (float)dt_max,
                                      (float)dmax, k == nb - 1 ? c->d_fire_left : nullptr, c->stream);
         }
+    };
+    const double key[5] = {f_tol, dt_max, dmax, (double)c->tpa, (double)c->cur};
+    if (c->use_graphs && (!c->fire_graph || !std::equal(key, key + 5, c->fire_key))) {
+        if (c->fire_graph) cudaGraphExecDestroy(c->fire_graph);
+        c->fire_graph = nullptr;
+        cudaGraph_t g = nullptr;
+        CKC(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_batch(batch);
+        CKC(c, cudaStreamEndCapture(c->stream, &g));
+        cudaError_t ce = cudaGraphInstantiate(&c->fire_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { c->fire_graph = nullptr; return fail(c, RC_ECUDA, "FIRE graph instantiation"); }
+        std::copy(key, key + 5, c->fire_key);
+    }
+    for (int it0 = 0; it0 < max_iter; it0 += batch) {
+        const int nb = std::min(batch, max_iter - it0);
+        if (c->use_graphs && nb == batch) CKC(c, cudaGraphLaunch(c->fire_graph, c->stream));
+        else enqueue_batch(nb);
         CKC(c, cudaGetLastError());
         int left = 0;
         CKC(c, cudaMemcpyAsync(&left, c->d_fire_left, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         CKC(c, cudaStreamSynchronize(c->stream));
         if (left == 0) break;
+    }
     }
     rc_launch_fire_zero_v(c->ka, c->fire, c->n_tiles, 1, c->stream);
     CKC(c, cudaGetLastError());
