@@ -593,7 +593,7 @@ def run_surrogate_train(args):
             "train_tflops": 3 * flop_fwd / (ms / 1e3) / 1e12,
             "predict_ms": ms_pred,
             "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_forward_fused (prediction)",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_forward_ws (prediction)",
                          "peak_source": peak_src}}
 
 

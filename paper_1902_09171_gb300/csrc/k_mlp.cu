@@ -384,24 +384,32 @@ void prepare_tc05() {
 // the batch (one member: blockIdx.y) and walks all T steps: per step the four
 // layers run back to back on the tensor cores, with the activations kept in
 // shared memory (BF16, K-major core-matrix layout) and the layer accumulator
-// (128 x 256 FP32) in tensor memory.  Weights (Wt, N x K) stream through four
-// shared buffers of 64 rows each: copies run three chunks ahead of the MMAs,
-// and a buffer is refilled once the MMAs that read it have completed (one
-// mbarrier per buffer, bounded waits).  Epilogues run in
-// 16 warps (warp w: accumulator rows 32 (w % 4).., column quarter w / 4): bias +
-// GELU into the next layer's operand; the head writes the stress and the new
-// state h = tanh(.) straight into the next step's input rows.  With a tape
-// (training) every step's z, y and a rows also go to global memory for the
-// backward pass, in the layout the layer-wise kernels use.
+// (128 x 256 FP32) in tensor memory.  The roles are split between warps:
+// one producer thread streams the weights through four shared buffers of 64
+// rows each with bulk copies (cp.async.bulk, one per chunk, completing on a
+// per-buffer mbarrier; the weights are pre-arranged per member by
+// k_pack_weights so that each chunk is one contiguous block in the buffer's
+// layout) and issues the MMAs; sixteen epilogue warps (warp w: accumulator
+// rows 32 (w % 4).., column quarter w / 4) wait for a layer's accumulator, run
+// its epilogue (bias + GELU into the next operand; the head writes the stress
+// and the new state h = tanh(.) straight into the next step's input rows) and
+// hand the operand back.  The two sides meet only at mbarriers, all waits
+// bounded:
+//   full[b]  : chunk in buffer b has landed          (bulk copy -> producer)
+//   empty[b] : the MMAs reading buffer b are done     (tcgen05.commit -> producer)
+//   acc      : a layer's accumulator is complete      (tcgen05.commit -> epilogue)
+//   epi      : the epilogue warps have written the next operand and read the
+//              accumulator (16 warp arrivals -> producer)
+// With a tape (training) every step's z, y and a rows also go to global memory
+// for the backward pass, in the layout the layer-wise kernels use.
 // ---------------------------------------------------------------------------
-constexpr int FT_THREADS = 512, FT_PARTS = FT_THREADS / 128, FT_M = 128, FT_NC = 64, FT_MAXK = 8;
+constexpr int FT_PARTS = 4, FT_M = 128, FT_NC = 64, FT_MAXK = 8;
 // The input rows z (128 x 144) and the activations (128 x 256) share one
 // buffer: z is dead once layer 1's MMAs have read it, and the head writes the
 // next step's state after the last layer's MMAs have read the activations.
-constexpr int FT_NBUF = 4;  // weight buffers: copies run up to three chunks ahead of the MMAs
+constexpr int FT_NBUF = 4;  // weight buffers
 constexpr int FT_SA = FT_M * WID * 2, FT_SW = FT_NC * WID * 2;
 constexpr int FT_SMEM = FT_SA + FT_NBUF * FT_SW;
-static_assert(FT_NBUF >= 2 && FT_NBUF <= 4, "cp_async_wait_upto covers up to two pending groups");
 constexpr int FT_CHUNKS = 4 + 4 + 4 + 3;  // weight chunks of 64 rows per step (N = 256, 256, 256, 144)
 
 struct FusedArgs {
@@ -415,60 +423,14 @@ struct FusedArgs {
     float *h;            // FP32 state (member k, row b at h + k * h_mstride + b * NH): read at step 0 and
     long h_mstride;      // overwritten with the final state; null: zero initial state, not written
     __nv_bfloat16 *tZ, *tY[3], *tA[3];  // tape (member 0 only), or null
-    const __nv_bfloat16 *Wt[FT_MAXK][4];
     const float *theta[FT_MAXK];
+    const unsigned char *Wp[FT_MAXK];  // packed weight chunks (k_pack_weights)
     int *err;
 };
 
 // byte offset of element (r, k) in a K-major core-matrix tile with `rows` rows
 __device__ __forceinline__ unsigned cm_off(int r, int k, int rows) {
     return (unsigned)((((k >> 3) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
-
-__device__ __forceinline__ unsigned mbar_try(unsigned bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done;
-}
-
-// every thread waits (bounded) for the phase with the given parity; the block
-// agrees on the outcome
-__device__ __forceinline__ bool mbar_wait_all(unsigned bar, unsigned parity) {
-    unsigned done = 0;
-    for (int it = 0; it < TC_SPIN && !done; it++) done = mbar_try(bar, parity);
-    return __syncthreads_and(done) != 0;
-}
-
-// copy weight chunk q (rows 64 q .. 64 q + 63 of the N x K matrix Wt, zero past N)
-// into a 64-row core-matrix buffer: all threads, one cp.async group
-__device__ __forceinline__ void ft_load_chunk(unsigned char *dst, const __nv_bfloat16 *Wt, int N, int K, int q) {
-    const int KC = K >> 3;
-    for (int idx = threadIdx.x; idx < FT_NC * KC; idx += FT_THREADS) {
-        const int r = idx / KC, kc = idx - r * KC, n = q * FT_NC + r;
-        const bool in = n < N;
-        const __nv_bfloat16 *src = Wt + (size_t)(in ? n : 0) * K + kc * 8;
-        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + cm_off(r, kc * 8, FT_NC));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// chunk c of the per-step weight sequence (layers 1..4, 64-row chunks) into buffer c % FT_NBUF
-__device__ __forceinline__ void ft_load_chunk_seq(unsigned char *sW, const __nv_bfloat16 *const *Wt, long c) {
-    const int j = (int)(c % FT_CHUNKS);
-    const int l = j < 4 ? 0 : (j < 8 ? 1 : (j < 12 ? 2 : 3)), q = j - 4 * l;
-    ft_load_chunk(sW + (c % FT_NBUF) * FT_SW, Wt[l], l == 3 ? N4 : WID, l == 0 ? K0 : WID, q);
-}
-
-// wait until at most n of this thread's copy groups are pending (0 <= n <= FT_NBUF - 2)
-__device__ __forceinline__ void cp_async_wait_upto(int n) {
-    if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
-    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 2;" ::: "memory");
 }
 
 __device__ __forceinline__ unsigned short bf16_bits(float v) {
@@ -495,19 +457,168 @@ __device__ __forceinline__ float gelu_as(float x) {
     return 0.5f * x * (1.0f + copysignf(erf_abs, x));
 }
 
-__global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
+constexpr int WS_EPI_WARPS = 16, WS_THREADS = (WS_EPI_WARPS + 1) * 32;
+constexpr int WS_CH0 = FT_NC * K0 * 2, WS_CH1 = FT_NC * WID * 2;  // chunk bytes of layer 1 / layers 2-4
+constexpr int WS_WP_BYTES = 4 * WS_CH0 + 11 * WS_CH1;              // packed weights per member
+static_assert(WS_EPI_WARPS == 4 * FT_PARTS, "epilogue warps cover 4 lane quarters x FT_PARTS column parts");
+
+// byte offset and size of chunk j (0..14) of one step's weight sequence
+__host__ __device__ __forceinline__ int ws_chunk_off(int j) { return j < 4 ? j * WS_CH0 : 4 * WS_CH0 + (j - 4) * WS_CH1; }
+__host__ __device__ __forceinline__ int ws_chunk_bytes(int j) { return j < 4 ? WS_CH0 : WS_CH1; }
+
+// Wt (N x K row-major, per layer) -> the 15 chunk images, zero rows past N
+__global__ void k_pack_weights(const __nv_bfloat16 *__restrict__ W0, const __nv_bfloat16 *__restrict__ W1,
+                               const __nv_bfloat16 *__restrict__ W2, const __nv_bfloat16 *__restrict__ W3,
+                               unsigned char *Wp) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte unit
+    const int u0 = 4 * FT_NC * (K0 / 8);                   // units of the layer-1 chunks
+    if (u >= u0 + 11 * FT_NC * (WID / 8)) return;
+    int j, idx;
+    if (u < u0) {
+        j = u / (FT_NC * (K0 / 8));
+        idx = u - j * FT_NC * (K0 / 8);
+    } else {
+        j = 4 + (u - u0) / (FT_NC * (WID / 8));
+        idx = (u - u0) - (j - 4) * FT_NC * (WID / 8);
+    }
+    const int l = j < 4 ? 0 : (j < 8 ? 1 : (j < 12 ? 2 : 3)), q = j - 4 * l;
+    const int K = l == 0 ? K0 : WID, N = l == 3 ? N4 : WID, KC = K / 8;
+    const __nv_bfloat16 *Wt = l == 0 ? W0 : (l == 1 ? W1 : (l == 2 ? W2 : W3));
+    const int r = idx / KC, kc = idx - r * KC, n = q * FT_NC + r;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (n < N) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)n * K + kc * 8);
+    *reinterpret_cast<uint4 *>(Wp + ws_chunk_off(j) + cm_off(r, kc * 8, FT_NC)) = v;
+}
+
+// Bounded wait that lets the hardware park the thread (up to WS_SUSPEND_NS per
+// try) instead of spinning, so that waiting warps leave the issue slots to the
+// producer and to the warps that have work: at most WS_TRIES tries (~2 s).
+constexpr unsigned WS_SUSPEND_NS = 100000;
+constexpr int WS_TRIES = 20000;
+
+__device__ __forceinline__ bool ws_wait(unsigned bar, unsigned parity) {
+    unsigned done = 0;
+    for (int it = 0; it < WS_TRIES && !done; it++)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity), "r"(WS_SUSPEND_NS)
+            : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void ws_bulk(unsigned char *sW, const unsigned char *Wp, long c, unsigned bar_full) {
+    const int j = (int)(c % FT_CHUNKS), b = (int)(c % FT_NBUF), bytes = ws_chunk_bytes(j);
+    const unsigned bar = bar_full + 8u * (unsigned)b;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sW + (size_t)b * FT_SW);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(Wp + ws_chunk_off(j)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// input rows of step t: columns 0..14 (u_t * u_inv) and the pad column, by `nthr` threads
+__device__ __forceinline__ void ws_build_u(const FusedArgs &a, unsigned char *sZ, int m0, int t, int tid, int nthr) {
+    const bool tape = a.tZ != nullptr;
+    for (int idx = tid; idx < FT_M * 16; idx += nthr) {
+        const int r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1, bb = m0 + r;
+        const float v = (j < NIN && bb < a.B) ? a.U[((size_t)bb * a.T + t) * NIN + j] * a.u_inv[j] : 0.0f;
+        const unsigned short hv = bf16_bits(v);
+        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = hv;
+        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ)[((size_t)t * a.B + bb) * K0 + col] = hv;
+    }
+}
+
+// the state columns of step 0 (given h, or zero)
+__device__ __forceinline__ void ws_build_h0(const FusedArgs &a, unsigned char *sZ, const float *h, int m0, int tid,
+                                            int nthr) {
+    const bool tape = a.tZ != nullptr;
+    for (int idx = tid; idx < FT_M * NH; idx += nthr) {
+        const int r = idx / NH, j = idx - r * NH, bb = m0 + r;
+        const float v = (h && bb < a.B) ? h[(size_t)bb * NH + j] : 0.0f;
+        const unsigned short hv = bf16_bits(v);
+        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = hv;
+        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ)[(size_t)bb * K0 + NIN + j] = hv;
+    }
+}
+
+// epilogue of layer l at step t for one warp: its 32 accumulator rows (lane
+// quarter), its column part, 16 columns at a time
+__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, int l, int t, int quarter, int part, int lane,
+                                            unsigned tmem, unsigned char *sZA, const float *s_bias, float *S, float *h,
+                                            int m0) {
+    const bool tape = a.tZ != nullptr;
+    const int B = a.B, T = a.T, row = quarter * 32 + lane, b = m0 + row;
+    const int Nl = l == 3 ? N4 : WID;
+    const int nch = Nl >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
+    for (int ch = ch0; ch < ch1; ch++) {
+        const int n0 = ch * 16;
+        unsigned r[16];
+        const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (l < 3) {
+            const float4 *bias = reinterpret_cast<const float4 *>(s_bias + l * WID + n0);
+            unsigned yp[8], ap[8];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+                const float4 bv = bias[j >> 2];
+                const float v0 = __uint_as_float(r[j]) + bv.x, v1 = __uint_as_float(r[j + 1]) + bv.y;
+                const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
+                yp[j >> 1] = bf16x2_bits(v0, v1);
+                yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
+                ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
+                ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
+            }
+            const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
+            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
+            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = a1;
+            if (tape && b < B) {
+                uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + ((size_t)t * B + b) * WID + n0);
+                uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + ((size_t)t * B + b) * WID + n0);
+                py[0] = make_uint4(yp[0], yp[1], yp[2], yp[3]);
+                py[1] = make_uint4(yp[4], yp[5], yp[6], yp[7]);
+                pa[0] = a0;
+                pa[1] = a1;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = n0 + j;
+                const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
+                if (n < NOUT) {
+                    if (b < B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
+                } else if (n < NOUT + NH) {
+                    const float hv = tanhf(o);
+                    const unsigned short hb = bf16_bits(hv);
+                    *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = hb;
+                    if (tape && b < B && t + 1 < T)
+                        reinterpret_cast<unsigned short *>(a.tZ)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] = hb;
+                    if (h && b < B && t + 1 == T) h[(size_t)b * NH + n - NOUT] = hv;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     extern __shared__ __align__(1024) unsigned char ft_smem[];
-    __shared__ __align__(8) unsigned long long s_bar[FT_NBUF];
+    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi;
     __shared__ unsigned s_tmem;
     __shared__ __align__(16) float s_bias[3 * WID + N4];  // b1, b2, b3, b4
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
-    unsigned char *sZ = ft_smem, *sA = ft_smem, *sW = ft_smem + FT_SA;
+    unsigned char *sZA = ft_smem, *sW = ft_smem + FT_SA;  // input rows and activations share the first 64 KB
     const float *theta = a.theta[mk];
     float *S = a.S + mk * a.s_mstride;
     float *h = a.h ? a.h + mk * a.h_mstride : nullptr;
-    const bool tape = a.tZ != nullptr;
-    const int B = a.B, T = a.T;
+    const int T = a.T;
 
     if (warp == 0) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
@@ -515,161 +626,104 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < 3 * WID + N4; i += FT_THREADS)
-        s_bias[i] = theta[i < WID ? OFF_B1 + i : (i < 2 * WID ? OFF_B2 + i - WID : (i < 3 * WID ? OFF_B3 + i - 2 * WID : OFF_B4 + i - 3 * WID))];
-    const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
+    for (int i = tid; i < 3 * WID + N4; i += WS_THREADS)
+        s_bias[i] = theta[i < WID ? OFF_B1 + i
+                                  : (i < 2 * WID ? OFF_B2 + i - WID
+                                                 : (i < 3 * WID ? OFF_B3 + i - 2 * WID : OFF_B4 + i - 3 * WID))];
+    const unsigned bar_full = (unsigned)__cvta_generic_to_shared(&s_full[0]);
+    const unsigned bar_empty = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
+    const unsigned bar_acc = (unsigned)__cvta_generic_to_shared(&s_acc);
+    const unsigned bar_epi = (unsigned)__cvta_generic_to_shared(&s_epi);
     if (tid == 0) {
-        for (int i = 0; i < FT_NBUF; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * i) : "memory");
+        for (int i = 0; i < FT_NBUF; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full + 8 * i) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_empty + 8 * i) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_acc) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_epi), "r"(WS_EPI_WARPS) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const long n_chunks = (long)T * FT_CHUNKS;
-    for (long c0 = 0; c0 < FT_NBUF - 1 && c0 < n_chunks; c0++) ft_load_chunk_seq(sW, a.Wt[mk], c0);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
-    long c = 0;  // chunks whose MMAs have been issued
     bool ok = true;
-    const int quarter = warp & 3, part = warp >> 2, row = quarter * 32 + lane, b = m0 + row;
 
-    for (int t = 0; t < T && ok; t++) {
-        // (a) input rows z_t = [u_t * u_inv, h (written by the head of step t-1; given or zero at
-        //     step 0), 0]
-        for (int idx = tid; idx < FT_M * 16; idx += FT_THREADS) {
-            const int r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1, bb = m0 + r;
-            const float v = (j < NIN && bb < B) ? a.U[((size_t)bb * T + t) * NIN + j] * a.u_inv[j] : 0.0f;
-            const unsigned short hv = bf16_bits(v);
-            *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = hv;
-            if (tape && bb < B) reinterpret_cast<unsigned short *>(a.tZ)[((size_t)t * B + bb) * K0 + col] = hv;
-        }
-        if (t == 0) {
-            for (int idx = tid; idx < FT_M * NH; idx += FT_THREADS) {
-                const int r = idx / NH, j = idx - r * NH, bb = m0 + r;
-                const float v = (h && bb < B) ? h[(size_t)bb * NH + j] : 0.0f;
-                const unsigned short hv = bf16_bits(v);
-                *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = hv;
-                if (tape && bb < B) reinterpret_cast<unsigned short *>(a.tZ)[(size_t)bb * K0 + NIN + j] = hv;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        // (b) the four layers
-        for (int l = 0; l < 4 && ok; l++) {
-            const int Kl = l == 0 ? K0 : WID, Nl = l == 3 ? N4 : WID, nq = l == 3 ? 3 : 4;
-            const unsigned aBase = (unsigned)__cvta_generic_to_shared(l == 0 ? sZ : sA);
-            for (int q = 0; q < nq && ok; q++, c++) {
-                // chunk c has landed (this thread's copies), and every thread's copies are visible
-                // to the tensor cores
-                cp_async_wait_upto((int)((c + FT_NBUF - 2 < n_chunks - 1 ? c + FT_NBUF - 2 : n_chunks - 1) - c));
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int buf = (int)(c % FT_NBUF);
-                if (tid == 0) {
-                    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
-                                           ((unsigned)(FT_M >> 4) << 24);
-                    const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + buf * FT_SW);
-                    const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
-                    const unsigned dcol = tmem + (unsigned)(q * FT_NC);
-                    for (int kk = 0; kk < (Kl >> 4); kk++) {
-                        const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
-                        const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
-                        const unsigned acc = kk > 0;
+    if (warp == WS_EPI_WARPS) {
+        // ---- producer: weight chunks and MMAs (one thread) ----
+        if (lane == 0) {
+            const unsigned char *Wp = a.Wp[mk];
+            const long n_chunks = (long)T * FT_CHUNKS;
+            for (long c0 = 0; c0 < FT_NBUF && c0 < n_chunks; c0++) ws_bulk(sW, Wp, c0, bar_full);
+            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
+                                   ((unsigned)(FT_M >> 4) << 24);
+            const unsigned aBase = (unsigned)__cvta_generic_to_shared(sZA);
+            const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
+            long c = 0;
+            for (int t = 0; t < T && ok; t++)
+                for (int l = 0; l < 4 && ok; l++) {
+                    // the layer's operand is in place and the accumulator has been read
+                    ok = ws_wait(bar_epi, (unsigned)((t * 4 + l) & 1));
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int Kl = l == 0 ? K0 : WID, nq = l == 3 ? 3 : 4;
+                    for (int q = 0; q < nq; q++, c++) {
+                        const int b = (int)(c % FT_NBUF);
+                        ok = ws_wait(bar_full + 8u * b, (unsigned)((c / FT_NBUF) & 1));
+                        if (!ok) break;
+                        const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + (size_t)b * FT_SW);
+                        const unsigned dcol = tmem + (unsigned)(q * FT_NC);
+                        for (int kk = 0; kk < (Kl >> 4); kk++) {
+                            const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
+                            const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
+                            const unsigned acc = kk > 0;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
                         asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                bar_empty + 8u * b)
                             : "memory");
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     bar0 + 8 * buf)
-                                 : "memory");
-                }
-                // refill the buffer of chunk c - 1 with chunk c + FT_NBUF - 1 once chunk c - 1's MMAs
-                // (its last reader) are done
-                if (c + FT_NBUF - 1 < n_chunks) {
-                    if (c >= 1) ok = mbar_wait_all(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
-                    if (ok) ft_load_chunk_seq(sW, a.Wt[mk], c + FT_NBUF - 1);
-                }
-            }
-            if (!ok) break;
-            // the layer's accumulator is complete once the MMAs of its last chunk are
-            ok = mbar_wait_all(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // (c) epilogue: this warp's 32 rows, its quarter of the columns, 16 at a time
-            const int nch = Nl >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
-            for (int ch = ch0; ch < ch1; ch++) {
-                const int n0 = ch * 16;
-                unsigned r[16];
-                const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];\n"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr)
-                    : "memory");
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (l < 3) {
-                    const float4 *bias = reinterpret_cast<const float4 *>(s_bias + l * WID + n0);
-                    unsigned yp[8], ap[8];  // BF16 pairs, low half = even column
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4) {
-                        const float4 bv = bias[j >> 2];
-                        const float v0 = __uint_as_float(r[j]) + bv.x, v1 = __uint_as_float(r[j + 1]) + bv.y;
-                        const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
-                        yp[j >> 1] = bf16x2_bits(v0, v1);
-                        yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
-                        ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
-                        ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
-                    }
-                    const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
-                    *reinterpret_cast<uint4 *>(sA + cm_off(row, n0, FT_M)) = a0;
-                    *reinterpret_cast<uint4 *>(sA + cm_off(row, n0 + 8, FT_M)) = a1;
-                    if (tape && b < B) {
-                        uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + ((size_t)t * B + b) * WID + n0);
-                        uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + ((size_t)t * B + b) * WID + n0);
-                        py[0] = make_uint4(yp[0], yp[1], yp[2], yp[3]);
-                        py[1] = make_uint4(yp[4], yp[5], yp[6], yp[7]);
-                        pa[0] = a0;
-                        pa[1] = a1;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int n = n0 + j;
-                        const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
-                        if (n < NOUT) {
-                            if (b < B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
-                        } else if (n < NOUT + NH) {
-                            const float hv = tanhf(o);
-                            const unsigned short hb = bf16_bits(hv);
-                            *reinterpret_cast<unsigned short *>(sZ + cm_off(row, NIN + n - NOUT, FT_M)) = hb;
-                            if (tape && b < B && t + 1 < T)
-                                reinterpret_cast<unsigned short *>(a.tZ)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] =
-                                    hb;
-                            if (h && b < B && t + 1 == T) h[(size_t)b * NH + n - NOUT] = hv;
+                        // refill the buffer of chunk c - 1 once the MMAs that read it are done
+                        if (c >= 1 && c - 1 + FT_NBUF < n_chunks) {
+                            const int pb = (int)((c - 1) % FT_NBUF);
+                            ok = ws_wait(bar_empty + 8u * pb, (unsigned)(((c - 1) / FT_NBUF) & 1));
+                            if (!ok) break;
+                            ws_bulk(sW, Wp, c - 1 + FT_NBUF, bar_full);
                         }
                     }
+                    if (!ok) break;
+                    // the accumulator is complete once every MMA issued so far is
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     bar_acc)
+                                 : "memory");
                 }
+            if (!ok) atomicExch(a.err, RC_ETIMEOUT);
+        }
+    } else {
+        // ---- epilogue warps ----
+        const int etid = tid, nthr = WS_EPI_WARPS * 32, quarter = warp & 3, part = warp >> 2;
+        ws_build_u(a, sZA, m0, 0, etid, nthr);
+        ws_build_h0(a, sZA, h, m0, etid, nthr);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+        for (int t = 0; t < T && ok; t++)
+            for (int l = 0; l < 4 && ok; l++) {
+                ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((t * 4 + l) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                ws_epilogue(a, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
+                if (l == 3 && t + 1 < T) ws_build_u(a, sZA, m0, t + 1, etid, nthr);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
             }
-            // the activations written above are read by the next MMAs (async proxy), and the
-            // accumulator is overwritten by them
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        }
-    }
-    if (!ok) {
-        if (tid == 0) atomicExch(a.err, RC_ETIMEOUT);
-        // let the tensor-core work and copies in flight finish before their memory is released
-        if (c >= 1) {
-            unsigned done = 0;
-            for (int it = 0; it < TC_SPIN && !done; it++)
-                done = mbar_try(bar0 + 8 * ((c - 1) % FT_NBUF), (unsigned)(((c - 1) / FT_NBUF) & 1));
-        }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!ok && lane == 0) atomicExch(a.err, RC_ETIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -679,8 +733,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_forward_fused(FusedArgs a) {
     }
 }
 
-void prepare_fused() {
-    cudaFuncSetAttribute(k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
+void prepare_ws() {
+    cudaFuncSetAttribute(k_forward_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
 }
 
 // ---------------------------------------------------------------------------
@@ -815,6 +869,7 @@ inline int cdiv(long a, int b) { return (int)((a + b - 1) / b); }
 struct SurMember {
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *W[4] = {nullptr}, *Wt[4] = {nullptr};
+    unsigned char *Wp = nullptr;  // weight chunks in the layout of the fused forward's shared buffers
     int step = 0;
 };
 
@@ -855,10 +910,12 @@ void cast_member(sur_ctx *s, SurMember &M) {
     for (int l = 0; l < 4; l++)
         k_cast_weights<<<cdiv((long)KDIM[l] * NDIM[l], 256), 256, 0, s->stream>>>(M.theta, M.W[l], M.Wt[l], WOFF[l],
                                                                                   KDIM[l], NDIM[l]);
+    const int units = WS_WP_BYTES / 16;
+    k_pack_weights<<<cdiv(units, 256), 256, 0, s->stream>>>(M.Wt[0], M.Wt[1], M.Wt[2], M.Wt[3], M.Wp);
 }
 
 // forward through T steps for member M; stress predictions into S (B x T x 6)
-// Whole-forward kernel for members k0 .. k0 + nk - 1 (see k_forward_fused).
+// Whole-forward kernel for members k0 .. k0 + nk - 1 (see k_forward_ws).
 void forward_fused(sur_ctx *s, int k0, int nk, const float *U, int B, int T, float *S, long s_mstride, int s_ld,
                    const float *s_mul, float *h, long h_mstride, bool tape) {
     for (int g = 0; g < nk; g += FT_MAXK) {
@@ -884,12 +941,12 @@ void forward_fused(sur_ctx *s, int k0, int nk, const float *U, int B, int T, flo
             a.tA[2] = s->A3;
         }
         for (int i = 0; i < ng; i++) {
-            for (int l = 0; l < 4; l++) a.Wt[i][l] = s->mem[k0 + g + i].Wt[l];
             a.theta[i] = s->mem[k0 + g + i].theta;
+            a.Wp[i] = s->mem[k0 + g + i].Wp;
         }
         a.err = s->d_err;
         dim3 grid(cdiv(B, FT_M), ng);
-        k_forward_fused<<<grid, FT_THREADS, FT_SMEM, s->stream>>>(a);
+        k_forward_ws<<<grid, WS_THREADS, FT_SMEM, s->stream>>>(a);
     }
 }
 
@@ -1039,7 +1096,7 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
     ok &= salloc(s, &s->loss_acc, 1) == cudaSuccess;
     ok &= salloc(s, &s->d_err, 1) == cudaSuccess;
     prepare_tc05();
-    prepare_fused();
+    prepare_ws();
     s->mem.resize(n_members);
     for (auto &M : s->mem) {
         ok &= salloc(s, &M.theta, NPAR) == cudaSuccess;
@@ -1050,6 +1107,7 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
             ok &= salloc(s, &M.W[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
             ok &= salloc(s, &M.Wt[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
         }
+        ok &= salloc(s, &M.Wp, (size_t)WS_WP_BYTES) == cudaSuccess;
     }
     if (!ok) { sur_destroy(s); return RC_ENOMEM; }
     float one[NIN];
