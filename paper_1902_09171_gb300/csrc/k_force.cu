@@ -131,15 +131,44 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
             if (gnn < ng) enn = __ldg(nb4 + (size_t)gnn * RC_TILE);
         }
         const int left = nn - 4 * g;
-        if (left >= 4) {  // full group
-            fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
-            fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
-            fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
-            fn(c3, rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS));
-        } else {  // the list's last, partial group
-            fn(c0, rc_disp(xi, c0, T, (unsigned)e.x >> RC_IDX_BITS));
-            if (left > 1) fn(c1, rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS));
-            if (left > 2) fn(c2, rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS));
+        // Warp-uniform fast paths for full groups: all four entries of the image
+        // slot 0 (the central image: x_j - x_i, the bits rc_disp gives for it) in
+        // every converged lane, or one image slot per lane's group (the runs of a
+        // stencil bin): one shift-table read and one x_i - sp per group instead of
+        // one per entry, the same arithmetic as rc_disp.
+        const unsigned s0 = (unsigned)e.x >> RC_IDX_BITS;
+        const bool one_slot =
+            left >= 4 && (((unsigned)(e.x ^ e.y) | (unsigned)(e.x ^ e.z) | (unsigned)(e.x ^ e.w)) >> RC_IDX_BITS) == 0;
+        const unsigned am = __activemask();
+        float3 d0, d1, d2, d3;
+        if (__all_sync(am, one_slot && s0 == RC_SLOT_CENTRAL)) {
+            d0 = rc_disp_central(xi, c0);
+            d1 = rc_disp_central(xi, c1);
+            d2 = rc_disp_central(xi, c2);
+            d3 = rc_disp_central(xi, c3);
+        } else if (__all_sync(am, one_slot)) {
+            const float4 sa = T.a[s0], sb = T.b[s0];
+            const float4 xs = make_float4(xi.x - sb.x, xi.y - sb.y, xi.z - sb.z, sb.w);
+            d0 = rc_disp_pre(c0, sa, xs);
+            d1 = rc_disp_pre(c1, sa, xs);
+            d2 = rc_disp_pre(c2, sa, xs);
+            d3 = rc_disp_pre(c3, sa, xs);
+        } else {  // mixed image slots, or the list's last, partial group (whose missing
+                  // entries repeat its first one: valid indices, results unused)
+            d0 = rc_disp(xi, c0, T, s0);
+            d1 = rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS);
+            d2 = rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS);
+            d3 = rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS);
+        }
+        if (left >= 4) {
+            fn(c0, d0);
+            fn(c1, d1);
+            fn(c2, d2);
+            fn(c3, d3);
+        } else {
+            fn(c0, d0);
+            if (left > 1) fn(c1, d1);
+            if (left > 2) fn(c2, d2);
         }
         if (gn >= ng) break;
         g = gn;
@@ -158,6 +187,8 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
 template <int TPA, bool M6, bool STG>
 __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, int cur) {
     extern __shared__ __align__(16) float4 s_cell[];
+    rc_pdl_wait();
+    rc_pdl_trigger();
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
@@ -232,6 +263,8 @@ template <int POT, int TPA, bool M6, bool STG, bool SAMPLE>
 __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KParams p, KArrays a, int cur, int mode, int slot,
                                                        int step_index) {
     extern __shared__ __align__(16) float4 s_cell[];
+    rc_pdl_wait();
+    rc_pdl_trigger();
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
@@ -360,7 +393,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
                 rc_set_status(a.status, c, RC_EBOND);
                 continue;
             }
-            const float3 dd = rc_disp(xi, xj, s_tab, (n0 + 1) + 3 * (n1 + 1) + 9 * (n2 + 1));
+            const float3 dd = rc_disp(xi, xj, s_tab, rc_image_slot(n0, n1, n2));
             const float dx = dd.x, dy = dd.y, dz = dd.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             if (!(r2 < p.R02)) {
@@ -530,7 +563,7 @@ __global__ void __launch_bounds__(RC_TILE) k_static_pk1(KParams p, KArrays a, in
                 const float f2 = Hi[5] * ez, f1 = Hi[3] * ey + Hi[4] * ez, f0 = Hi[0] * ex + Hi[1] * ey + Hi[2] * ez;
                 const int n0 = -(int)rintf(f0), n1 = -(int)rintf(f1), n2 = -(int)rintf(f2);
                 if (n0 < -1 || n0 > 1 || n1 < -1 || n1 > 1 || n2 < -1 || n2 > 1) continue;
-                const float3 dd = rc_disp(xi, xj, s_tab, (n0 + 1) + 3 * (n1 + 1) + 9 * (n2 + 1));
+                const float3 dd = rc_disp(xi, xj, s_tab, rc_image_slot(n0, n1, n2));
                 const float r2 = fmaf(dd.x, dd.x, fmaf(dd.y, dd.y, dd.z * dd.z));
                 if (!(r2 < p.R02)) continue;
                 float gr = p.k_fene / (1.0f - r2 / p.R02);
@@ -554,10 +587,10 @@ template <int POT, bool M6, bool STG, bool SAMPLE>
 void launch_force_tpa(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
                       int step_index, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: k_force<POT, 1, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 2: k_force<POT, 2, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    case 4: k_force<POT, 4, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur, mode, slot, step_index); break;
-    default: k_force<POT, 8, M6, STG, SAMPLE><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur, mode, slot, step_index); break;
+    case 1: rc_launch_pdl(k_force<POT, 1, M6, STG, SAMPLE>, n_tiles, RC_TILE * 1, smem, s, p, a, cur, mode, slot, step_index); break;
+    case 2: rc_launch_pdl(k_force<POT, 2, M6, STG, SAMPLE>, n_tiles, RC_TILE * 2, smem, s, p, a, cur, mode, slot, step_index); break;
+    case 4: rc_launch_pdl(k_force<POT, 4, M6, STG, SAMPLE>, n_tiles, RC_TILE * 4, smem, s, p, a, cur, mode, slot, step_index); break;
+    default: rc_launch_pdl(k_force<POT, 8, M6, STG, SAMPLE>, n_tiles, RC_TILE * 8, smem, s, p, a, cur, mode, slot, step_index); break;
     }
 }
 
@@ -573,10 +606,10 @@ void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, 
 template <bool M6, bool STG>
 void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: k_density<1, M6, STG><<<n_tiles, RC_TILE * 1, smem, s>>>(p, a, cur); break;
-    case 2: k_density<2, M6, STG><<<n_tiles, RC_TILE * 2, smem, s>>>(p, a, cur); break;
-    case 4: k_density<4, M6, STG><<<n_tiles, RC_TILE * 4, smem, s>>>(p, a, cur); break;
-    default: k_density<8, M6, STG><<<n_tiles, RC_TILE * 8, smem, s>>>(p, a, cur); break;
+    case 1: rc_launch_pdl(k_density<1, M6, STG>, n_tiles, RC_TILE * 1, smem, s, p, a, cur); break;
+    case 2: rc_launch_pdl(k_density<2, M6, STG>, n_tiles, RC_TILE * 2, smem, s, p, a, cur); break;
+    case 4: rc_launch_pdl(k_density<4, M6, STG>, n_tiles, RC_TILE * 4, smem, s, p, a, cur); break;
+    default: rc_launch_pdl(k_density<8, M6, STG>, n_tiles, RC_TILE * 8, smem, s, p, a, cur); break;
     }
 }
 

@@ -59,6 +59,8 @@ __device__ int block_exclusive_scan(int *s, int n) {
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int cur) {
+    rc_pdl_wait();
+    rc_pdl_trigger();
     const int c = blockIdx.x;
     __shared__ int s_cnt[RC_MAX_BINS_PER_CELL];
     __shared__ int s_go;
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
 }
 
 __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur) {
+    rc_pdl_wait();
+    rc_pdl_trigger();
     const int t = blockIdx.x;
     const int c = a.tile_cell[t];
     if (!a.built[c]) return;
@@ -200,20 +204,20 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                 for (int o2 = -1; o2 <= 1; o2++) {
                     int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
                     u2 -= s2 * nb2;
-                    const int code = (s0 + 1) + 3 * (s1 + 1) + 9 * (s2 + 1);
-                    if ((code == RC_CODE_CENTRAL) != (sweep == 0)) continue;
+                    const int slot = rc_image_slot(s0, s1, s2);
+                    if ((slot == RC_SLOT_CENTRAL) != (sweep == 0)) continue;
                     const int bb = (u0 * nb1 + u1) * nb2 + u2;
                     const int j0 = bs[bb], j1 = bs[bb + 1];
                     for (int jl = j0; jl < j1; jl++) {
-                        if (jl == li && code == RC_CODE_CENTRAL) continue;
+                        if (jl == li && slot == RC_SLOT_CENTRAL) continue;
                         if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
                         const float4 xj = X[off + jl];
-                        const float3 d = rc_disp(xi, xj, s_tab, code);
+                        const float3 d = rc_disp(xi, xj, s_tab, slot);
                         const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
                         if (r2 < p.rlist2) {
                             if (cnt < p.max_nb)
                                 nbr[(size_t)(cnt >> 2) * (4 * RC_TILE) + (cnt & 3)] =
-                                    (int)((unsigned)(off + jl) | ((unsigned)code << RC_IDX_BITS));
+                                    (int)((unsigned)(off + jl) | ((unsigned)slot << RC_IDX_BITS));
                             cnt++;
                         }
                     }
@@ -231,9 +235,9 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
 }  // namespace
 
 void rc_launch_sort(const KParams &p, const KArrays &a, int cur, int n_cells, cudaStream_t s) {
-    k_sort<<<n_cells, SORT_THREADS, 0, s>>>(p, a, cur);
+    rc_launch_pdl(k_sort, n_cells, SORT_THREADS, 0, s, p, a, cur);
 }
 
 void rc_launch_nlist(const KParams &p, const KArrays &a, int cur, int n_tiles, cudaStream_t s) {
-    k_nlist<<<n_tiles, RC_TILE, 0, s>>>(p, a, cur);
+    rc_launch_pdl(k_nlist, n_tiles, RC_TILE, 0, s, p, a, cur);
 }

@@ -115,27 +115,37 @@ __device__ __forceinline__ void rc_set_status(int *status, int cell, int code) {
 
 // Periodic image shift tables.  The MD box H is stored FP32-exact (the FP64
 // box of the deformation is rounded once), so the Cartesian shift
-// sh = H (sx, sy, sz) of image code (sx+1) + 3(sy+1) + 9(sz+1) is exact in FP64
+// sh = H (sx, sy, sz) of image (sx, sy, sz), s in {-1, 0, 1}, is exact in FP64
 // and split into an FP32 value plus an FP32 remainder `lo` (nonzero only for
 // combinations of tilted box vectors).  The displacement x_j + sh - x_i is then
 // formed as ((x_j + sn) - (x_i - sp)) + lo with sn = min(sh, 0), sp = max(sh, 0):
 // x_j + sn and x_i - sp subtract numbers of similar size (exact), so only the
 // final subtraction rounds -- the result is the correctly rounded displacement
 // instead of one carrying an error of half an ulp of the box length.
-// Per image code: a = {min(sh,0) (3), lo.x}, b = {max(sh,0) (3), lo.y}; the z
+// Per image slot: a = {min(sh,0) (3), lo.x}, b = {max(sh,0) (3), lo.y}; the z
 // shift n2 * H_zz is exact in FP32, so lo.z = 0.  Two 16-byte shared loads per pair.
+//
+// Images are numbered by slot k = (code + 14) mod 27 of the image code
+// code = (sx+1) + 3(sy+1) + 9(sz+1): the central image (code 13) is slot 0, so
+// a list entry j | k << RC_IDX_BITS of the central image is the bare index j.
 struct ShiftTab {
     float4 a[27], b[27];
 };
 
-__device__ __forceinline__ void rc_build_shift(ShiftTab &T, const float *H, int code) {
+constexpr int RC_SLOT_CENTRAL = 0;
+__host__ __device__ __forceinline__ int rc_image_slot(int sx, int sy, int sz) {
+    return ((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1) + 14) % 27;
+}
+
+__device__ __forceinline__ void rc_build_shift(ShiftTab &T, const float *H, int slot) {
+    const int code = (slot + 13) % 27;
     const double sx = (double)(code % 3 - 1), sy = (double)((code / 3) % 3 - 1), sz = (double)(code / 9 - 1);
     const double hx = (double)H[0] * sx + (double)H[1] * sy + (double)H[2] * sz;
     const double hy = (double)H[3] * sy + (double)H[4] * sz;
     const double hz = (double)H[5] * sz;
     const float fx = (float)hx, fy = (float)hy, fz = (float)hz;
-    T.a[code] = make_float4(fminf(fx, 0.f), fminf(fy, 0.f), fminf(fz, 0.f), (float)(hx - fx));
-    T.b[code] = make_float4(fmaxf(fx, 0.f), fmaxf(fy, 0.f), fmaxf(fz, 0.f), (float)(hy - fy));
+    T.a[slot] = make_float4(fminf(fx, 0.f), fminf(fy, 0.f), fminf(fz, 0.f), (float)(hx - fx));
+    T.b[slot] = make_float4(fmaxf(fx, 0.f), fmaxf(fy, 0.f), fmaxf(fz, 0.f), (float)(hy - fy));
 }
 
 // fill the table from cell c's box (call with all threads; syncs)
@@ -146,16 +156,49 @@ __device__ __forceinline__ void rc_load_shifts(ShiftTab &T, float *s_H, const fl
     __syncthreads();
 }
 
-// The central image (code 13) has all-zero table entries, so its displacement is
-// x_j - x_i bit for bit.  Lists hold their central entries first: lanes of a
-// warp then mostly read the same (central) entry, which shared memory serves
-// as one broadcast.
-constexpr int RC_CODE_CENTRAL = 13;
-
-__device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, const ShiftTab &T, int code) {
-    const float4 sa = T.a[code], sb = T.b[code];
+// The central image has all-zero table entries, so its displacement is
+// x_j - x_i bit for bit (rc_disp_central).  Lists hold their central entries
+// first, so the lanes of a warp walk long runs of central entries together.
+__device__ __forceinline__ float3 rc_disp(const float4 &xi, const float4 &xj, const ShiftTab &T, int slot) {
+    const float4 sa = T.a[slot], sb = T.b[slot];
     return make_float3(((xj.x + sa.x) - (xi.x - sb.x)) + sa.w, ((xj.y + sa.y) - (xi.y - sb.y)) + sb.w,
                        (xj.z + sa.z) - (xi.z - sb.z));
+}
+
+// rc_disp with the slot's entries sa = T.a[slot] and xs = {x_i - T.b[slot] (3),
+// T.b[slot].w} formed once for several neighbours of the same image slot
+__device__ __forceinline__ float3 rc_disp_pre(const float4 &xj, const float4 &sa, const float4 &xs) {
+    return make_float3(((xj.x + sa.x) - xs.x) + sa.w, ((xj.y + sa.y) - xs.y) + xs.w, (xj.z + sa.z) - xs.z);
+}
+
+__device__ __forceinline__ float3 rc_disp_central(const float4 &xi, const float4 &xj) {
+    return make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z);
+}
+
+// Programmatic dependent launch of the MD-step kernels (sort, list, density,
+// force): each is launched with programmatic stream serialisation, so that its
+// CTAs can be scheduled while the previous kernel of the stream drains, and
+// begins with rc_pdl_wait(), which returns once that kernel has completed and
+// its memory operations are visible -- before any access to shared state.  It
+// then allows its own dependent to be scheduled (rc_pdl_trigger).  Launched
+// without the attribute, the wait returns at once.
+__device__ __forceinline__ void rc_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void rc_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+void rc_launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                   Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // per-cell state of the FIRE minimiser (k_fire.cu)
