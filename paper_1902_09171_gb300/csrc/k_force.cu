@@ -90,6 +90,29 @@ __device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, in
 
 // Slots of a list group past the end of the list hold stale data: point them at
 // the group's first entry, which is always valid, so that they can be gathered.
+// List groups are read once per pass: loaded without allocating in L1, which
+// then keeps the neighbour records that the atoms of a tile share.
+__device__ __forceinline__ int4 ld_list(const int4 *p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// Tile order of the pair kernels.  The grid is padded to a multiple R of the
+// SM count S, and block b takes tile (b mod S) R + b / S: blocks b, b + S,
+// b + 2S, ... -- those that the first wave deals to one SM -- get consecutive
+// tiles, the spatial neighbours of one r-cell, whose shared neighbour records
+// then stay in that SM's L1.  Blocks past the last tile return at once.
+__device__ __forceinline__ int tile_of_block(int n_sm) {
+    const int R = (int)gridDim.x / n_sm;
+    return (int)(blockIdx.x % n_sm) * R + (int)(blockIdx.x / n_sm);
+}
+inline unsigned pair_grid(const KParams &p) {
+    return (unsigned)(((p.n_tiles + p.n_sm - 1) / p.n_sm) * p.n_sm);
+}
+
 __device__ __forceinline__ int4 clamp_group(int4 e, int left) {
     if (left < 4) {
         if (left < 2) e.y = e.x;
@@ -112,12 +135,12 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
     const int ng = (nn + 3) >> 2;
     int g = sub;
     if (g >= ng) return;
-    int4 e = clamp_group(__ldg(nb4 + (size_t)g * RC_TILE), nn - 4 * g);
+    int4 e = clamp_group(ld_list(nb4 + (size_t)g * RC_TILE), nn - 4 * g);
     float4 c0 = src((unsigned)e.x & RC_IDX_MASK), c1 = src((unsigned)e.y & RC_IDX_MASK);
     float4 c2 = src((unsigned)e.z & RC_IDX_MASK), c3 = src((unsigned)e.w & RC_IDX_MASK);
     int gn = g + TPA;
     int4 en = e;
-    if (gn < ng) en = __ldg(nb4 + (size_t)gn * RC_TILE);
+    if (gn < ng) en = ld_list(nb4 + (size_t)gn * RC_TILE);
     while (true) {
         const int gnn = gn + TPA;
         float4 n0 = c0, n1 = c1, n2 = c2, n3 = c3;
@@ -128,7 +151,7 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
             n1 = src((unsigned)en.y & RC_IDX_MASK);
             n2 = src((unsigned)en.z & RC_IDX_MASK);
             n3 = src((unsigned)en.w & RC_IDX_MASK);
-            if (gnn < ng) enn = __ldg(nb4 + (size_t)gnn * RC_TILE);
+            if (gnn < ng) enn = ld_list(nb4 + (size_t)gnn * RC_TILE);
         }
         const int left = nn - 4 * g;
         // Warp-uniform fast paths for full groups: all four entries of the image
@@ -189,7 +212,8 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     extern __shared__ __align__(16) float4 s_cell[];
     rc_pdl_wait();
     rc_pdl_trigger();
-    const int t = blockIdx.x;
+    const int t = tile_of_block(p.n_sm);
+    if (t >= p.n_tiles) return;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
     __shared__ ShiftTab s_tab;
@@ -265,7 +289,8 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     extern __shared__ __align__(16) float4 s_cell[];
     rc_pdl_wait();
     rc_pdl_trigger();
-    const int t = blockIdx.x;
+    const int t = tile_of_block(p.n_sm);
+    if (t >= p.n_tiles) return;
     const int c = a.tile_cell[t];
     if (a.status[c] != 0 || !a.active[c]) return;
     __shared__ ShiftTab s_tab;
@@ -587,10 +612,10 @@ template <int POT, bool M6, bool STG, bool SAMPLE>
 void launch_force_tpa(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
                       int step_index, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: rc_launch_pdl(k_force<POT, 1, M6, STG, SAMPLE>, n_tiles, RC_TILE * 1, smem, s, p, a, cur, mode, slot, step_index); break;
-    case 2: rc_launch_pdl(k_force<POT, 2, M6, STG, SAMPLE>, n_tiles, RC_TILE * 2, smem, s, p, a, cur, mode, slot, step_index); break;
-    case 4: rc_launch_pdl(k_force<POT, 4, M6, STG, SAMPLE>, n_tiles, RC_TILE * 4, smem, s, p, a, cur, mode, slot, step_index); break;
-    default: rc_launch_pdl(k_force<POT, 8, M6, STG, SAMPLE>, n_tiles, RC_TILE * 8, smem, s, p, a, cur, mode, slot, step_index); break;
+    case 1: rc_launch_pdl(k_force<POT, 1, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur, mode, slot, step_index); break;
+    case 2: rc_launch_pdl(k_force<POT, 2, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 2, smem, s, p, a, cur, mode, slot, step_index); break;
+    case 4: rc_launch_pdl(k_force<POT, 4, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 4, smem, s, p, a, cur, mode, slot, step_index); break;
+    default: rc_launch_pdl(k_force<POT, 8, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 8, smem, s, p, a, cur, mode, slot, step_index); break;
     }
 }
 
@@ -606,10 +631,10 @@ void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, 
 template <bool M6, bool STG>
 void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int smem, cudaStream_t s) {
     switch (tpa) {
-    case 1: rc_launch_pdl(k_density<1, M6, STG>, n_tiles, RC_TILE * 1, smem, s, p, a, cur); break;
-    case 2: rc_launch_pdl(k_density<2, M6, STG>, n_tiles, RC_TILE * 2, smem, s, p, a, cur); break;
-    case 4: rc_launch_pdl(k_density<4, M6, STG>, n_tiles, RC_TILE * 4, smem, s, p, a, cur); break;
-    default: rc_launch_pdl(k_density<8, M6, STG>, n_tiles, RC_TILE * 8, smem, s, p, a, cur); break;
+    case 1: rc_launch_pdl(k_density<1, M6, STG>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur); break;
+    case 2: rc_launch_pdl(k_density<2, M6, STG>, pair_grid(p), RC_TILE * 2, smem, s, p, a, cur); break;
+    case 4: rc_launch_pdl(k_density<4, M6, STG>, pair_grid(p), RC_TILE * 4, smem, s, p, a, cur); break;
+    default: rc_launch_pdl(k_density<8, M6, STG>, pair_grid(p), RC_TILE * 8, smem, s, p, a, cur); break;
     }
 }
 

@@ -47,6 +47,8 @@ struct KParams {
     uint64_t seed;
     int max_nb;
     float max_step;       // > 0: displacement limit per step
+    int n_tiles;          // tiles of RC_TILE atoms in the batch
+    int n_sm;             // SMs of the device (tile order of the pair kernels)
 };
 
 struct KArrays {

@@ -272,6 +272,10 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     kp.mvv2e = (float)(P.mass / ftm2v);
     kp.seed = P.seed;
     kp.max_nb = max_nb;
+    kp.n_tiles = c->n_tiles;
+    kp.n_sm = 1;
+    CKC(c, cudaDeviceGetAttribute(&kp.n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    if (kp.n_sm < 1) kp.n_sm = 1;
     kp.max_step = P.max_step > 0 ? (float)P.max_step : 0.0f;
 
     // ---- device memory ----
