@@ -155,9 +155,9 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one k_force<SC> launch on this workload (128 000
 # atoms, skin 1.5 A), from an ncu capture of the current kernel (--set full,
-# the non-sampling variant): 123.04 MB read + 4.59 MB written.  Mostly the
+# the non-sampling variant): 121.91 MB read + 2.83 MB written.  Mostly the
 # Verlet list, re-read from DRAM every launch.
-K_FORCE_DRAM_BYTES = 127.63e6
+K_FORCE_DRAM_BYTES = 124.75e6
 
 
 def fp32_unit_peak_tflops():
