@@ -45,7 +45,17 @@ struct Epi {
     __nv_bfloat16 *h_next;   // HEAD: next step's input row block (columns NIN..NIN+NH), may be null
     float *h_f32;            // HEAD: FP32 copy of h (ld NH), may be null
     const float *s_mul;      // HEAD: per-component stress scale (null: network units)
+    long ms_in, ms_out;      // member strides (elements) of y_in and of the outputs, for member-batched launches
 };
+
+// the epilogue pointers of member z of a member-batched launch
+__device__ __forceinline__ void epi_member(Epi &e, int z) {
+    if (z == 0) return;
+    if (e.y_in) e.y_in += z * e.ms_in;
+    if (e.y_out) e.y_out += z * e.ms_out;
+    if (e.a_out) e.a_out += z * e.ms_out;
+    if (e.s_out) e.s_out += z * e.ms_out;
+}
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x) {
@@ -129,13 +139,17 @@ __device__ __forceinline__ void epilogue16(const Epi &e, int m, int n, int M, in
 template <int EPI, bool TRANS_A>
 __global__ void __launch_bounds__(GEMM_THREADS) k_gemm(const __nv_bfloat16 *__restrict__ A, int lda,
                                                        const __nv_bfloat16 *__restrict__ B, int ldb, int M, int N,
-                                                       int K, int k_chunk, Epi e) {
+                                                       int K, int k_chunk, Epi e, int nz, long a_ms, long b_ms) {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PADK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, q = lane & 3;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kb = blockIdx.z * k_chunk, ke = min(K, kb + k_chunk);
+    const int mb = blockIdx.z / nz;  // member of a member-batched launch, then the split-K part
+    A += mb * a_ms;
+    B += mb * b_ms;
+    epi_member(e, mb);
+    const int kb = (blockIdx.z - mb * nz) * k_chunk, ke = min(K, kb + k_chunk);
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -211,14 +225,15 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm(const __nv_bfloat16 *__re
         }
 }
 
+// nb members at once (operand strides a_ms, b_ms; epilogue strides in e)
 template <int EPI, bool TRANS_A>
 void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K,
-          const Epi &e, int split_k = 1) {
+          const Epi &e, int split_k = 1, int nb = 1, long a_ms = 0, long b_ms = 0) {
     int chunk = (K + split_k - 1) / split_k;
     chunk = (chunk + BK - 1) / BK * BK;
     const int nz = (K + chunk - 1) / chunk;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nz);
-    k_gemm<EPI, TRANS_A><<<grid, GEMM_THREADS, 0, s>>>(A, lda, B, ldb, M, N, K, chunk, e);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nz * nb);
+    k_gemm<EPI, TRANS_A><<<grid, GEMM_THREADS, 0, s>>>(A, lda, B, ldb, M, N, K, chunk, e, nz, a_ms, b_ms);
 }
 
 // ---------------------------------------------------------------------------
@@ -249,12 +264,15 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 template <int EPI>
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *__restrict__ A, int lda,
                                                           const __nv_bfloat16 *__restrict__ Bk, int ldb, int M, int N,
-                                                          int K, Epi e, int *err) {
+                                                          int K, Epi e, int *err, long a_ms, long b_ms) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+    A += blockIdx.z * a_ms;  // member of a member-batched launch
+    Bk += blockIdx.z * b_ms;
+    epi_member(e, blockIdx.z);
     const int KC = K >> 3;  // 16-byte chunks along K
     unsigned char *sA = tc_smem, *sB = tc_smem + (size_t)TC_M * K * 2;
     // tensor memory: 64 columns x 128 lanes of FP32 for the 128 x 64 accumulator
@@ -362,13 +380,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *_
     }
 }
 
-// C = A[M x K] * Bk[N x K]^T on tcgen05 (K a multiple of 16, K <= 256)
+// C = A[M x K] * Bk[N x K]^T on tcgen05 (K a multiple of 16, K <= 256), for nb
+// members at once (operand strides a_ms, b_ms; epilogue strides in e)
 template <int EPI>
 void gemm_tc05(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bk, int ldb, int M, int N, int K,
-               const Epi &e, int *err) {
-    dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M);
+               const Epi &e, int *err, int nb = 1, long a_ms = 0, long b_ms = 0) {
+    dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, nb);
     const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
-    k_gemm_tc05<EPI><<<grid, TC_THREADS, smem, s>>>(A, lda, Bk, ldb, M, N, K, e, err);
+    k_gemm_tc05<EPI><<<grid, TC_THREADS, smem, s>>>(A, lda, Bk, ldb, M, N, K, e, err, a_ms, b_ms);
 }
 
 void prepare_tc05() {
@@ -422,7 +441,8 @@ struct FusedArgs {
     int s_ld;
     float *h;            // FP32 state (member k, row b at h + k * h_mstride + b * NH): read at step 0 and
     long h_mstride;      // overwritten with the final state; null: zero initial state, not written
-    __nv_bfloat16 *tZ, *tY[3], *tA[3];  // tape (member 0 only), or null
+    __nv_bfloat16 *tZ, *tY[3], *tA[3];  // tape of the launch's first member, or null
+    long tz_ms, ty_ms;                   // member strides (elements) of tZ and of tY / tA
     const float *theta[FT_MAXK];
     const unsigned char *Wp[FT_MAXK];  // packed weight chunks (k_pack_weights)
     int *err;
@@ -518,35 +538,36 @@ __device__ __forceinline__ void ws_bulk(unsigned char *sW, const unsigned char *
 }
 
 // input rows of step t: columns 0..14 (u_t * u_inv) and the pad column, by `nthr` threads
-__device__ __forceinline__ void ws_build_u(const FusedArgs &a, unsigned char *sZ, int m0, int t, int tid, int nthr) {
+__device__ __forceinline__ void ws_build_u(const FusedArgs &a, long tzo, unsigned char *sZ, int m0, int t, int tid,
+                                           int nthr) {
     const bool tape = a.tZ != nullptr;
     for (int idx = tid; idx < FT_M * 16; idx += nthr) {
         const int r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1, bb = m0 + r;
         const float v = (j < NIN && bb < a.B) ? a.U[((size_t)bb * a.T + t) * NIN + j] * a.u_inv[j] : 0.0f;
         const unsigned short hv = bf16_bits(v);
         *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = hv;
-        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ)[((size_t)t * a.B + bb) * K0 + col] = hv;
+        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ + tzo)[((size_t)t * a.B + bb) * K0 + col] = hv;
     }
 }
 
 // the state columns of step 0 (given h, or zero)
-__device__ __forceinline__ void ws_build_h0(const FusedArgs &a, unsigned char *sZ, const float *h, int m0, int tid,
-                                            int nthr) {
+__device__ __forceinline__ void ws_build_h0(const FusedArgs &a, long tzo, unsigned char *sZ, const float *h, int m0,
+                                            int tid, int nthr) {
     const bool tape = a.tZ != nullptr;
     for (int idx = tid; idx < FT_M * NH; idx += nthr) {
         const int r = idx / NH, j = idx - r * NH, bb = m0 + r;
         const float v = (h && bb < a.B) ? h[(size_t)bb * NH + j] : 0.0f;
         const unsigned short hv = bf16_bits(v);
         *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = hv;
-        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ)[(size_t)bb * K0 + NIN + j] = hv;
+        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ + tzo)[(size_t)bb * K0 + NIN + j] = hv;
     }
 }
 
 // epilogue of layer l at step t for one warp: its 32 accumulator rows (lane
 // quarter), its column part, 16 columns at a time
-__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, int l, int t, int quarter, int part, int lane,
-                                            unsigned tmem, unsigned char *sZA, const float *s_bias, float *S, float *h,
-                                            int m0) {
+__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tzo, long tyo, int l, int t, int quarter,
+                                            int part, int lane, unsigned tmem, unsigned char *sZA,
+                                            const float *s_bias, float *S, float *h, int m0) {
     const bool tape = a.tZ != nullptr;
     const int B = a.B, T = a.T, row = quarter * 32 + lane, b = m0 + row;
     const int Nl = l == 3 ? N4 : WID;
@@ -580,8 +601,8 @@ __device__ __forceinline__ void ws_epilogue(const FusedArgs &a, int l, int t, in
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = a1;
             if (tape && b < B) {
-                uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + ((size_t)t * B + b) * WID + n0);
-                uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + ((size_t)t * B + b) * WID + n0);
+                uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + tyo + ((size_t)t * B + b) * WID + n0);
+                uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + tyo + ((size_t)t * B + b) * WID + n0);
                 py[0] = make_uint4(yp[0], yp[1], yp[2], yp[3]);
                 py[1] = make_uint4(yp[4], yp[5], yp[6], yp[7]);
                 pa[0] = a0;
@@ -599,7 +620,7 @@ __device__ __forceinline__ void ws_epilogue(const FusedArgs &a, int l, int t, in
                     const unsigned short hb = bf16_bits(hv);
                     *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = hb;
                     if (tape && b < B && t + 1 < T)
-                        reinterpret_cast<unsigned short *>(a.tZ)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] = hb;
+                        reinterpret_cast<unsigned short *>(a.tZ + tzo)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] = hb;
                     if (h && b < B && t + 1 == T) h[(size_t)b * NH + n - NOUT] = hv;
                 }
             }
@@ -614,6 +635,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     __shared__ __align__(16) float s_bias[3 * WID + N4];  // b1, b2, b3, b4
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
+    const long tzo = mk * a.tz_ms, tyo = mk * a.ty_ms;  // this member's tape
     unsigned char *sZA = ft_smem, *sW = ft_smem + FT_SA;  // input rows and activations share the first 64 KB
     const float *theta = a.theta[mk];
     float *S = a.S + mk * a.s_mstride;
@@ -706,8 +728,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     } else {
         // ---- epilogue warps ----
         const int etid = tid, nthr = WS_EPI_WARPS * 32, quarter = warp & 3, part = warp >> 2;
-        ws_build_u(a, sZA, m0, 0, etid, nthr);
-        ws_build_h0(a, sZA, h, m0, etid, nthr);
+        ws_build_u(a, tzo, sZA, m0, 0, etid, nthr);
+        ws_build_h0(a, tzo, sZA, h, m0, etid, nthr);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
@@ -716,8 +738,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((t * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                ws_epilogue(a, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
-                if (l == 3 && t + 1 < T) ws_build_u(a, sZA, m0, t + 1, etid, nthr);
+                ws_epilogue(a, tzo, tyo, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
+                if (l == 3 && t + 1 < T) ws_build_u(a, tzo, sZA, m0, t + 1, etid, nthr);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -752,10 +774,18 @@ __global__ void k_build_input(const float *__restrict__ U, int B, int T, int t, 
 }
 
 // head gradient do_t = [scale (s - y/s_scale), dh (1 - h^2), 0]; loss partials
-__global__ void k_head_grad(const float *__restrict__ S, const float *__restrict__ Y, int B, int T, int t,
-                            const float *__restrict__ s_inv, const __nv_bfloat16 *__restrict__ Hrow,
-                            const float *__restrict__ dZ, int have_dh, float gscale, __nv_bfloat16 *dO,
-                            double *loss_acc) {
+// Member blockIdx.y of a member-batched launch: S, Hrow, dZ and dO advance by
+// their member strides, loss_acc by one.
+__global__ void k_head_grad(const float *__restrict__ S, long s_ms, const float *__restrict__ Y, int B, int T, int t,
+                            const float *__restrict__ s_inv, const __nv_bfloat16 *__restrict__ Hrow, long h_ms,
+                            const float *__restrict__ dZ, long dz_ms, int have_dh, float gscale, __nv_bfloat16 *dO,
+                            long do_ms, double *loss_acc) {
+    const int z = blockIdx.y;
+    S += z * s_ms;
+    Hrow += z * h_ms;
+    dZ += z * dz_ms;
+    dO += z * do_ms;
+    loss_acc += z;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.0f;
     if (idx < B * N4) {
@@ -777,8 +807,11 @@ __global__ void k_head_grad(const float *__restrict__ S, const float *__restrict
     if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss_acc, (double)l);
 }
 
-// column sums of a [rows x N] bf16 matrix into g (FP32, accumulate)
-__global__ void k_colsum(const __nv_bfloat16 *__restrict__ X, long rows, int N, float *g) {
+// column sums of a [rows x N] bf16 matrix into g (FP32, accumulate); member
+// blockIdx.z at X + z x_ms, g + z g_ms
+__global__ void k_colsum(const __nv_bfloat16 *__restrict__ X, long rows, int N, float *g, long x_ms, long g_ms) {
+    X += blockIdx.z * x_ms;
+    g += blockIdx.z * g_ms;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const long r0 = (long)blockIdx.y * 2048, r1 = min(rows, r0 + 2048);
@@ -885,11 +918,17 @@ struct sur_ctx {
     std::vector<void *> allocs;
     float *u_inv = nullptr, *s_inv = nullptr, *s_mul = nullptr;
     float h_u_scale[NIN], h_s_scale[NOUT];
-    // activations (T x B rows)
+    // activations (T x B rows), one slice per member (member strides zs, ys, os, dzs
+    // elements), so that the members train side by side
     __nv_bfloat16 *Z = nullptr, *Y1 = nullptr, *A1 = nullptr, *Y2 = nullptr, *A2 = nullptr, *Y3 = nullptr,
                   *A3 = nullptr, *dO = nullptr, *dY3 = nullptr, *dY2 = nullptr, *dY1 = nullptr;
+    long zs = 0, ys = 0, os = 0, dzs = 0;
     float *S = nullptr, *dZ = nullptr, *Sm = nullptr;
-    double *loss_acc = nullptr;
+    double *loss_acc = nullptr;  // one per member
+    // parameters of all members, member after member (the SurMember pointers point into these)
+    float *theta_all = nullptr, *grad_all = nullptr, *m_all = nullptr, *v_all = nullptr;
+    __nv_bfloat16 *W_all[4] = {nullptr}, *Wt_all[4] = {nullptr};
+    unsigned char *Wp_all = nullptr;
 };
 
 namespace {
@@ -931,14 +970,17 @@ void forward_fused(sur_ctx *s, int k0, int nk, const float *U, int B, int T, flo
         a.s_ld = s_ld;
         a.h = h ? h + (size_t)g * h_mstride : nullptr;
         a.h_mstride = h_mstride;
-        if (tape) {
-            a.tZ = s->Z;
-            a.tY[0] = s->Y1;
-            a.tY[1] = s->Y2;
-            a.tY[2] = s->Y3;
-            a.tA[0] = s->A1;
-            a.tA[1] = s->A2;
-            a.tA[2] = s->A3;
+        if (tape) {  // the members' own tape slices
+            const long k = k0 + g;
+            a.tZ = s->Z + k * s->zs;
+            a.tY[0] = s->Y1 + k * s->ys;
+            a.tY[1] = s->Y2 + k * s->ys;
+            a.tY[2] = s->Y3 + k * s->ys;
+            a.tA[0] = s->A1 + k * s->ys;
+            a.tA[1] = s->A2 + k * s->ys;
+            a.tA[2] = s->A3 + k * s->ys;
+            a.tz_ms = s->zs;
+            a.ty_ms = s->ys;
         }
         for (int i = 0; i < ng; i++) {
             a.theta[i] = s->mem[k0 + g + i].theta;
@@ -950,21 +992,24 @@ void forward_fused(sur_ctx *s, int k0, int nk, const float *U, int B, int T, flo
     }
 }
 
-void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, const float *s_mul) {
+// forward through T steps for member k, its tape into the member's slice
+void forward(sur_ctx *s, int k, const float *U, int B, int T, float *S, const float *s_mul) {
     if (s->backend == 2) {
-        const int k = (int)(&M - s->mem.data());
         forward_fused(s, k, 1, U, B, T, S, 0, T * NOUT, s_mul, nullptr, 0, true);
         return;
     }
+    SurMember &M = s->mem[k];
     const size_t RB = (size_t)B;
+    __nv_bfloat16 *Zk = s->Z + k * s->zs;
+    __nv_bfloat16 *Ys[3] = {s->Y1 + k * s->ys, s->Y2 + k * s->ys, s->Y3 + k * s->ys};
+    __nv_bfloat16 *As_[3] = {s->A1 + k * s->ys, s->A2 + k * s->ys, s->A3 + k * s->ys};
     for (int t = 0; t < T; t++) {
-        __nv_bfloat16 *Zt = s->Z + (size_t)t * RB * K0;
+        __nv_bfloat16 *Zt = Zk + (size_t)t * RB * K0;
         k_build_input<<<cdiv(RB * K0, 256), 256, 0, s->stream>>>(U, B, T, t, s->u_inv, Zt, t == 0);
         Epi e{};
         e.ld_out = WID;
         const __nv_bfloat16 *in = Zt;
         int kin = K0;
-        __nv_bfloat16 *Ys[3] = {s->Y1, s->Y2, s->Y3}, *As_[3] = {s->A1, s->A2, s->A3};
         for (int l = 0; l < 3; l++) {
             e.bias = M.theta + BOFF[l];
             e.y_out = Ys[l] + (size_t)t * RB * WID;
@@ -979,59 +1024,87 @@ void forward(sur_ctx *s, SurMember &M, const float *U, int B, int T, float *S, c
         h.s_out = S + (size_t)t * NOUT;
         h.s_ld = T * NOUT;
         h.s_mul = s_mul;  // null during training: the loss works in network units
-        h.h_next = (t + 1 < T) ? s->Z + (size_t)(t + 1) * RB * K0 : nullptr;
+        h.h_next = (t + 1 < T) ? Zk + (size_t)(t + 1) * RB * K0 : nullptr;
         h.h_f32 = nullptr;
         if (s->backend) gemm_tc05<EPI_HEAD>(s->stream, in, WID, M.Wt[3], WID, B, N4, WID, h, s->d_err);
         else gemm<EPI_HEAD, false>(s->stream, in, WID, M.W[3], N4, B, N4, WID, h);
     }
 }
 
-// BPTT: gradient into M.grad (zeroed here); returns nothing (loss into loss_acc)
-void backward(sur_ctx *s, SurMember &M, const float *Y, int B, int T, const float *S) {
+// BPTT for members k0 .. k0 + nk - 1 at once (their tape slices; predictions S
+// of member k0 + i at S + i s_ms): gradients into their grad blocks (zeroed
+// here), loss partial sums into loss_acc[k0 + i]
+void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, const float *S, long s_ms) {
     const size_t RB = (size_t)B;
-    cudaMemsetAsync(M.grad, 0, sizeof(float) * NPAR, s->stream);
+    cudaMemsetAsync(s->grad_all + (size_t)k0 * NPAR, 0, sizeof(float) * NPAR * nk, s->stream);
     const float gscale = 2.0f / ((float)B * T * NOUT);
+    const long ys = s->ys;
+    __nv_bfloat16 *Z = s->Z + k0 * s->zs, *dO = s->dO + k0 * s->os;
+    __nv_bfloat16 *Y1 = s->Y1 + k0 * ys, *Y2 = s->Y2 + k0 * ys, *Y3 = s->Y3 + k0 * ys;
+    __nv_bfloat16 *A1 = s->A1 + k0 * ys, *A2 = s->A2 + k0 * ys, *A3 = s->A3 + k0 * ys;
+    __nv_bfloat16 *dY1 = s->dY1 + k0 * ys, *dY2 = s->dY2 + k0 * ys, *dY3 = s->dY3 + k0 * ys;
+    float *dZ = s->dZ + k0 * s->dzs;
+    const __nv_bfloat16 *W[4], *Wt[4];
+    long wms[4];
+    for (int l = 0; l < 4; l++) {
+        wms[l] = (long)KDIM[l] * NDIM[l];
+        W[l] = s->W_all[l] + k0 * wms[l];
+        Wt[l] = s->Wt_all[l] + k0 * wms[l];
+    }
+    const bool tc = s->backend != 0;
     for (int t = T - 1; t >= 0; t--) {
-        __nv_bfloat16 *dOt = s->dO + (size_t)t * RB * N4;
-        const __nv_bfloat16 *Hrow = (t + 1 < T) ? s->Z + (size_t)(t + 1) * RB * K0 : s->Z;
-        k_head_grad<<<cdiv(RB * N4, 256), 256, 0, s->stream>>>(S, Y, B, T, t, s->s_inv, Hrow, s->dZ, t + 1 < T,
-                                                              gscale, dOt, s->loss_acc);
+        __nv_bfloat16 *dOt = dO + (size_t)t * RB * N4;
+        const __nv_bfloat16 *Hrow = (t + 1 < T) ? Z + (size_t)(t + 1) * RB * K0 : Z;
+        k_head_grad<<<dim3(cdiv(RB * N4, 256), nk), 256, 0, s->stream>>>(S, s_ms, Y, B, T, t, s->s_inv, Hrow, s->zs,
+                                                                         dZ, s->dzs, t + 1 < T, gscale, dOt, s->os,
+                                                                         s->loss_acc + k0);
         Epi e{};
         e.ld_out = WID;
         e.ld_in = WID;
+        e.ms_in = ys;
+        e.ms_out = ys;
         // dY3 = (dO W4^T) * gelu'(Y3)
-        e.y_in = s->Y3 + (size_t)t * RB * WID;
-        e.a_out = s->dY3 + (size_t)t * RB * WID;
-        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, dOt, N4, M.W[3], N4, B, WID, N4, e, s->d_err);
-        else gemm<EPI_DGELU, false>(s->stream, dOt, N4, M.Wt[3], WID, B, WID, N4, e);
-        e.y_in = s->Y2 + (size_t)t * RB * WID;
-        e.a_out = s->dY2 + (size_t)t * RB * WID;
-        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.W[2], WID, B, WID, WID, e, s->d_err);
-        else gemm<EPI_DGELU, false>(s->stream, s->dY3 + (size_t)t * RB * WID, WID, M.Wt[2], WID, B, WID, WID, e);
-        e.y_in = s->Y1 + (size_t)t * RB * WID;
-        e.a_out = s->dY1 + (size_t)t * RB * WID;
-        if (s->backend) gemm_tc05<EPI_DGELU>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.W[1], WID, B, WID, WID, e, s->d_err);
-        else gemm<EPI_DGELU, false>(s->stream, s->dY2 + (size_t)t * RB * WID, WID, M.Wt[1], WID, B, WID, WID, e);
+        e.y_in = Y3 + (size_t)t * RB * WID;
+        e.a_out = dY3 + (size_t)t * RB * WID;
+        if (tc) gemm_tc05<EPI_DGELU>(s->stream, dOt, N4, W[3], N4, B, WID, N4, e, s->d_err, nk, s->os, wms[3]);
+        else gemm<EPI_DGELU, false>(s->stream, dOt, N4, Wt[3], WID, B, WID, N4, e, 1, nk, s->os, wms[3]);
+        e.y_in = Y2 + (size_t)t * RB * WID;
+        e.a_out = dY2 + (size_t)t * RB * WID;
+        const __nv_bfloat16 *g3 = dY3 + (size_t)t * RB * WID;
+        if (tc) gemm_tc05<EPI_DGELU>(s->stream, g3, WID, W[2], WID, B, WID, WID, e, s->d_err, nk, ys, wms[2]);
+        else gemm<EPI_DGELU, false>(s->stream, g3, WID, Wt[2], WID, B, WID, WID, e, 1, nk, ys, wms[2]);
+        e.y_in = Y1 + (size_t)t * RB * WID;
+        e.a_out = dY1 + (size_t)t * RB * WID;
+        const __nv_bfloat16 *g2 = dY2 + (size_t)t * RB * WID;
+        if (tc) gemm_tc05<EPI_DGELU>(s->stream, g2, WID, W[1], WID, B, WID, WID, e, s->d_err, nk, ys, wms[1]);
+        else gemm<EPI_DGELU, false>(s->stream, g2, WID, Wt[1], WID, B, WID, WID, e, 1, nk, ys, wms[1]);
         if (t > 0) {  // dZ = dY1 W1^T (only the state part is used by step t-1)
             Epi f{};
-            f.s_out = s->dZ;
+            f.s_out = dZ;
             f.s_ld = K0;
-            if (s->backend) gemm_tc05<EPI_F32>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.W[0], WID, B, K0, WID, f, s->d_err);
-            else gemm<EPI_F32, false>(s->stream, s->dY1 + (size_t)t * RB * WID, WID, M.Wt[0], K0, B, K0, WID, f);
+            f.ms_out = s->dzs;
+            const __nv_bfloat16 *g1 = dY1 + (size_t)t * RB * WID;
+            if (tc) gemm_tc05<EPI_F32>(s->stream, g1, WID, W[0], WID, B, K0, WID, f, s->d_err, nk, ys, wms[0]);
+            else gemm<EPI_F32, false>(s->stream, g1, WID, Wt[0], K0, B, K0, WID, f, 1, nk, ys, wms[0]);
         }
     }
     // weight gradients over all steps at once: dW = op(A_all)^T dY_all (split-K)
     const long rows = (long)T * B;
     const int split = (int)std::min<long>(16, std::max<long>(1, rows / 4096));
-    const __nv_bfloat16 *Ain[4] = {s->Z, s->A1, s->A2, s->A3};
-    const __nv_bfloat16 *dOut[4] = {s->dY1, s->dY2, s->dY3, s->dO};
+    const __nv_bfloat16 *Ain[4] = {Z, A1, A2, A3};
+    const long ams[4] = {s->zs, ys, ys, ys};
+    const __nv_bfloat16 *dOut[4] = {dY1, dY2, dY3, dO};
+    const long dms[4] = {ys, ys, ys, s->os};
+    float *grad = s->grad_all + (size_t)k0 * NPAR;
     for (int l = 0; l < 4; l++) {
         Epi w{};
-        w.s_out = M.grad + WOFF[l];
+        w.s_out = grad + WOFF[l];
         w.s_ld = NDIM[l];
-        gemm<EPI_WGRAD, true>(s->stream, Ain[l], KDIM[l], dOut[l], NDIM[l], KDIM[l], NDIM[l], (int)rows, w, split);
-        dim3 g(cdiv(NDIM[l], 128), cdiv(rows, 2048));
-        k_colsum<<<g, 128, 0, s->stream>>>(dOut[l], rows, NDIM[l], M.grad + BOFF[l]);
+        w.ms_out = NPAR;
+        gemm<EPI_WGRAD, true>(s->stream, Ain[l], KDIM[l], dOut[l], NDIM[l], KDIM[l], NDIM[l], (int)rows, w, split, nk,
+                              ams[l], dms[l]);
+        dim3 g(cdiv(NDIM[l], 128), cdiv(rows, 2048), nk);
+        k_colsum<<<g, 128, 0, s->stream>>>(dOut[l], rows, NDIM[l], grad + BOFF[l], dms[l], NPAR);
     }
 }
 
@@ -1081,35 +1154,49 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
     if (stream) s->stream = (cudaStream_t)stream;
     else if (cudaStreamCreate(&s->stream) != cudaSuccess) { delete s; return RC_ECUDA; }
     else s->own_stream = true;
-    const size_t R = (size_t)max_batch * max_steps;
+    const size_t R = (size_t)max_batch * max_steps, Kn = (size_t)n_members;
+    s->zs = (long)(R * K0 + (size_t)max_batch * K0);
+    s->ys = (long)(R * WID);
+    s->os = (long)(R * N4);
+    s->dzs = (long)max_batch * K0;
     bool ok = true;
     ok &= salloc(s, &s->u_inv, NIN) == cudaSuccess;
     ok &= salloc(s, &s->s_inv, NOUT) == cudaSuccess;
     ok &= salloc(s, &s->s_mul, NOUT) == cudaSuccess;
-    ok &= salloc(s, &s->Z, R * K0 + (size_t)max_batch * K0) == cudaSuccess;
+    ok &= salloc(s, &s->Z, Kn * s->zs) == cudaSuccess;
     for (__nv_bfloat16 **p : {&s->Y1, &s->A1, &s->Y2, &s->A2, &s->Y3, &s->A3, &s->dY3, &s->dY2, &s->dY1})
-        ok &= salloc(s, p, R * WID) == cudaSuccess;
-    ok &= salloc(s, &s->dO, R * N4) == cudaSuccess;
-    ok &= salloc(s, &s->S, R * NOUT * (size_t)n_members) == cudaSuccess;
-    ok &= salloc(s, &s->Sm, (size_t)max_batch * NOUT * n_members) == cudaSuccess;
-    ok &= salloc(s, &s->dZ, (size_t)max_batch * K0) == cudaSuccess;
-    ok &= salloc(s, &s->loss_acc, 1) == cudaSuccess;
+        ok &= salloc(s, p, Kn * s->ys) == cudaSuccess;
+    ok &= salloc(s, &s->dO, Kn * s->os) == cudaSuccess;
+    ok &= salloc(s, &s->S, R * NOUT * Kn) == cudaSuccess;
+    ok &= salloc(s, &s->Sm, (size_t)max_batch * NOUT * Kn) == cudaSuccess;
+    ok &= salloc(s, &s->dZ, Kn * s->dzs) == cudaSuccess;
+    ok &= salloc(s, &s->loss_acc, Kn) == cudaSuccess;
     ok &= salloc(s, &s->d_err, 1) == cudaSuccess;
+    ok &= salloc(s, &s->theta_all, Kn * NPAR) == cudaSuccess;
+    ok &= salloc(s, &s->grad_all, Kn * NPAR) == cudaSuccess;
+    ok &= salloc(s, &s->m_all, Kn * NPAR) == cudaSuccess;
+    ok &= salloc(s, &s->v_all, Kn * NPAR) == cudaSuccess;
+    for (int l = 0; l < 4; l++) {
+        ok &= salloc(s, &s->W_all[l], Kn * KDIM[l] * NDIM[l]) == cudaSuccess;
+        ok &= salloc(s, &s->Wt_all[l], Kn * KDIM[l] * NDIM[l]) == cudaSuccess;
+    }
+    ok &= salloc(s, &s->Wp_all, Kn * WS_WP_BYTES) == cudaSuccess;
+    if (!ok) { sur_destroy(s); return RC_ENOMEM; }
     prepare_tc05();
     prepare_ws();
     s->mem.resize(n_members);
-    for (auto &M : s->mem) {
-        ok &= salloc(s, &M.theta, NPAR) == cudaSuccess;
-        ok &= salloc(s, &M.grad, NPAR) == cudaSuccess;
-        ok &= salloc(s, &M.m, NPAR) == cudaSuccess;
-        ok &= salloc(s, &M.v, NPAR) == cudaSuccess;
+    for (size_t k = 0; k < Kn; k++) {
+        SurMember &M = s->mem[k];
+        M.theta = s->theta_all + k * NPAR;
+        M.grad = s->grad_all + k * NPAR;
+        M.m = s->m_all + k * NPAR;
+        M.v = s->v_all + k * NPAR;
         for (int l = 0; l < 4; l++) {
-            ok &= salloc(s, &M.W[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
-            ok &= salloc(s, &M.Wt[l], (size_t)KDIM[l] * NDIM[l]) == cudaSuccess;
+            M.W[l] = s->W_all[l] + k * KDIM[l] * NDIM[l];
+            M.Wt[l] = s->Wt_all[l] + k * KDIM[l] * NDIM[l];
         }
-        ok &= salloc(s, &M.Wp, (size_t)WS_WP_BYTES) == cudaSuccess;
+        M.Wp = s->Wp_all + k * WS_WP_BYTES;
     }
-    if (!ok) { sur_destroy(s); return RC_ENOMEM; }
     float one[NIN];
     for (int k = 0; k < NIN; k++) one[k] = 1.0f;
     if (sur_set_scaling(s, one, one) != RC_OK) { sur_destroy(s); return RC_ECUDA; }
@@ -1168,11 +1255,12 @@ int sur_loss_grad(sur_ctx *s, int member, const float *U, const float *Y, int B,
     if (!s || !U || !Y || member < 0 || member >= s->K) return RC_EINVAL;
     if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
     SurMember &M = s->mem[member];
-    cudaMemsetAsync(s->loss_acc, 0, sizeof(double), s->stream);
-    forward(s, M, U, B, T, s->S, nullptr);
-    backward(s, M, Y, B, T, s->S);
+    float *Sk = s->S + (size_t)member * B * T * NOUT;
+    cudaMemsetAsync(s->loss_acc + member, 0, sizeof(double), s->stream);
+    forward(s, member, U, B, T, Sk, nullptr);
+    backward_members(s, member, 1, Y, B, T, Sk, 0);
     double l = 0.0;
-    cudaMemcpyAsync(&l, s->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(&l, s->loss_acc + member, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (grad) cudaMemcpyAsync(grad, M.grad, sizeof(float) * NPAR, cudaMemcpyDeviceToHost, s->stream);
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return RC_ECUDA;
     if (loss) *loss = l / ((double)B * T * NOUT);
@@ -1182,21 +1270,29 @@ int sur_loss_grad(sur_ctx *s, int member, const float *U, const float *Y, int B,
 int sur_train_step(sur_ctx *s, const float *U, const float *Y, int B, int T, float lr, float wd, double *loss) {
     if (!s || !U || !Y) return RC_EINVAL;
     if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
-    std::vector<double> l(s->K, 0.0);
+    const long s_ms = (long)B * T * NOUT;
+    cudaMemsetAsync(s->loss_acc, 0, sizeof(double) * s->K, s->stream);
+    if (s->backend == 2) {  // every member at once: one fused forward, member-batched backward launches
+        forward_fused(s, 0, s->K, U, B, T, s->S, s_ms, T * NOUT, nullptr, nullptr, 0, true);
+        backward_members(s, 0, s->K, Y, B, T, s->S, s_ms);
+    } else {
+        for (int k = 0; k < s->K; k++) {
+            forward(s, k, U, B, T, s->S + k * s_ms, nullptr);
+            backward_members(s, k, 1, Y, B, T, s->S + k * s_ms, 0);
+        }
+    }
     for (int k = 0; k < s->K; k++) {
         SurMember &M = s->mem[k];
-        cudaMemsetAsync(s->loss_acc, 0, sizeof(double), s->stream);
-        forward(s, M, U, B, T, s->S, nullptr);
-        backward(s, M, Y, B, T, s->S);
         M.step++;
         const float b1 = 0.9f, b2 = 0.999f;
         const float bc1 = 1.0f - std::pow(b1, (float)M.step), bc2 = 1.0f - std::pow(b2, (float)M.step);
         k_adamw<<<cdiv(NPAR, 256), 256, 0, s->stream>>>(M.theta, M.grad, M.m, M.v, NPAR, lr, wd, b1, b2, bc1, bc2,
                                                         1e-8f);
         cast_member(s, M);
-        if (loss) cudaMemcpyAsync(&l[k], s->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     }
     if (loss) {
+        std::vector<double> l(s->K, 0.0);
+        cudaMemcpyAsync(l.data(), s->loss_acc, sizeof(double) * s->K, cudaMemcpyDeviceToHost, s->stream);
         if (cudaStreamSynchronize(s->stream) != cudaSuccess) return RC_ECUDA;
         for (int k = 0; k < s->K; k++) loss[k] = l[k] / ((double)B * T * NOUT);
     }
@@ -1210,7 +1306,7 @@ int sur_predict(sur_ctx *s, const float *U, int B, int T, float *Sout) {
         forward_fused(s, 0, s->K, U, B, T, Sout, (long)B * T * NOUT, T * NOUT, s->s_mul, nullptr, 0, false);
         return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
     }
-    for (int k = 0; k < s->K; k++) forward(s, s->mem[k], U, B, T, Sout + (size_t)k * B * T * NOUT, s->s_mul);
+    for (int k = 0; k < s->K; k++) forward(s, k, U, B, T, Sout + (size_t)k * B * T * NOUT, s->s_mul);
     return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
 }
 
