@@ -755,9 +755,203 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradients on tcgen05: G[Kd x Nd] += sum over rows r of X[r][m] D[r][n]
+// (X: the layer inputs of every step, rows x Kd; D: the output gradients,
+// rows x Nd; both row-major, Kd, Nd <= 256 and multiples of 16).  Both
+// operands are the transposed (MN-major) kind for the tensor core: a 16-byte
+// piece of a row (8 consecutive m, or n) is one row of a core matrix, so the
+// rows stream into shared memory with plain 16-byte asynchronous copies.
+// Core matrix (mn/8, r/8) of a stage sits at byte (r/8 * MN/8 + mn/8) * 128,
+// piece r%8 at +16 (r%8); the descriptors take the stride between core
+// matrices along r as the leading and along mn as the stride byte offset, as
+// for the K-major operands of the other kernels.  A CTA owns a range of rows
+// and the whole output: two 128-row accumulators (m < 128, m >= 128) of up to
+// 256 FP32 columns each fill the 512 columns of tensor memory; a three-stage
+// pipeline of 64-row chunks (X 32 KB + D 32 KB per stage) keeps the copies of
+// the next chunks in flight while the MMAs of the current one run; the partial
+// sums are added into G (FP32 atomics).  Member blockIdx.y of a member-batched
+// launch reads X + y x_ms, D + y d_ms and adds into G + y g_ms.
+// ---------------------------------------------------------------------------
+constexpr int WG_ROWS = 64, WG_STAGES = 3, WG_THREADS = 128;
+constexpr int WG_SX = 256 * WG_ROWS * 2, WG_SD = 256 * WG_ROWS * 2, WG_STAGE = WG_SX + WG_SD;
+constexpr int WG_SMEM = WG_STAGES * WG_STAGE;
+
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_tc05(const __nv_bfloat16 *__restrict__ X, long x_ms, int Kd, const __nv_bfloat16 *__restrict__ D,
+                 long d_ms, int Nd, long rows, long rows_per_cta, float *G, long g_ms, int *err) {
+    extern __shared__ __align__(1024) unsigned char wg_smem[];
+    __shared__ __align__(8) unsigned long long s_done[WG_STAGES];
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    X += blockIdx.y * x_ms;
+    D += blockIdx.y * d_ms;
+    G += blockIdx.y * g_ms;
+    const long r_begin = (long)blockIdx.x * rows_per_cta;
+    const long r_end = r_begin + rows_per_cta < rows ? r_begin + rows_per_cta : rows;
+    const int n_chunks = r_end > r_begin ? (int)((r_end - r_begin + WG_ROWS - 1) / WG_ROWS) : 0;
+    const int MH = Kd > 128 ? 2 : 1;  // accumulators (m < 128, m >= 128)
+    const int XC = Kd >> 3, DC = Nd >> 3;  // 16-byte pieces per row
+
+    if (warp == 0) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < WG_STAGES; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((unsigned)__cvta_generic_to_shared(&s_done[i]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // chunk c into its stage: X rows as 128-row halves [MH][...], D rows; pieces
+    // past the matrix (rows, columns) are zero-filled
+    auto load_chunk = [&](int c) {
+        unsigned char *sx = wg_smem + (size_t)(c % WG_STAGES) * WG_STAGE, *sd = sx + WG_SX;
+        const long r0 = r_begin + (long)c * WG_ROWS;
+        for (int idx = tid; idx < WG_ROWS * 32; idx += WG_THREADS) {  // X: 64 rows x 32 pieces (256 columns)
+            const int rr = idx >> 5, pc = idx & 31, m = pc * 8, h = m >> 7, mm = m & 127;
+            if (h >= MH) continue;
+            const long r = r0 + rr;
+            const bool in = r < r_end && pc < XC;
+            const __nv_bfloat16 *src = X + (in ? r * Kd + m : 0);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(
+                sx + (size_t)h * (128 * WG_ROWS * 2) + ((rr >> 3) * 16 + (mm >> 3)) * 128 + (rr & 7) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                         : "memory");
+        }
+        for (int idx = tid; idx < WG_ROWS * DC; idx += WG_THREADS) {  // D: 64 rows x Nd/8 pieces
+            const int rr = idx / DC, pc = idx - rr * DC;
+            const long r = r0 + rr;
+            const bool in = r < r_end;
+            const __nv_bfloat16 *src = D + (in ? r * Nd + pc * 8 : 0);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(sd + ((rr >> 3) * DC + pc) * 128 + (rr & 7) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                         : "memory");
+        }
+    };
+    for (int c = 0; c < WG_STAGES - 1; c++) {
+        if (c < n_chunks) load_chunk(c);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, both transposed (MN-major), N/8, M/16
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((unsigned)(Nd >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+    const unsigned lboX = 16 * 128, lboD = (unsigned)DC * 128;  // between core matrices along r
+    bool ok = true;
+    int issued = -1;  // last chunk whose MMAs were issued
+    for (int c = 0; c < n_chunks && ok; c++) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(WG_STAGES - 2) : "memory");
+        __syncthreads();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sx = (unsigned)__cvta_generic_to_shared(wg_smem + (size_t)(c % WG_STAGES) * WG_STAGE);
+            const unsigned sd = sx + WG_SX;
+            for (int h = 0; h < MH; h++)
+                for (int ks = 0; ks < WG_ROWS / 16; ks++) {
+                    const uint64_t ad = tc_desc(sx + h * (128 * WG_ROWS * 2) + ks * 2 * lboX, lboX, 128);
+                    const uint64_t bd = tc_desc(sd + ks * 2 * lboD, lboD, 128);
+                    const unsigned acc = (c > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (unsigned)(h * 256)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(&s_done[c % WG_STAGES]))
+                         : "memory");
+        }
+        issued = c;
+        // the stage of chunk c - 1 takes chunk c + STAGES - 1 once its MMAs are done
+        const int cn = c + WG_STAGES - 1;
+        if (cn < n_chunks) {
+            if (c >= 1) {
+                const int cp = c - 1;
+                ok = ws_wait((unsigned)__cvta_generic_to_shared(&s_done[cp % WG_STAGES]),
+                             (unsigned)((cp / WG_STAGES) & 1));
+            }
+            if (ok) load_chunk(cn);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        ok = __syncthreads_and(ok);
+    }
+    // the accumulators are complete once the last chunk's MMAs are
+    if (ok && n_chunks > 0) {
+        const int cl = n_chunks - 1;
+        ok = ws_wait((unsigned)__cvta_generic_to_shared(&s_done[cl % WG_STAGES]), (unsigned)((cl / WG_STAGES) & 1));
+    }
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && n_chunks > 0) {
+        for (int h = 0; h < MH; h++) {
+            const int m = h * 128 + warp * 32 + lane;
+            for (int c0 = 0; c0 < Nd; c0 += 16) {
+                unsigned r[16];
+                const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(h * 256 + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < Kd) {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) atomicAdd(&G[(size_t)m * Nd + c0 + j], __uint_as_float(r[j]));
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, RC_ETIMEOUT);
+        // let the copies and MMAs in flight finish before the memory is released
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (tid == 0)
+            for (int c = issued >= WG_STAGES ? issued - WG_STAGES + 1 : 0; c <= issued; c++)
+                ws_wait((unsigned)__cvta_generic_to_shared(&s_done[c % WG_STAGES]), (unsigned)((c / WG_STAGES) & 1));
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
 void prepare_ws() {
     cudaFuncSetAttribute(k_forward_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
+    cudaFuncSetAttribute(k_wgrad_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
 }
+
+int g_n_sm = 0;
+
+// the weight gradients of nb members: G_i += X_i^T D_i over `rows` rows, about
+// one CTA per SM in all
+void wgrad_tc05(cudaStream_t st, const __nv_bfloat16 *X, long x_ms, int Kd, const __nv_bfloat16 *D, long d_ms, int Nd,
+                long rows, float *G, long g_ms, int nb, int *err) {
+    if (g_n_sm <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (g_n_sm <= 0) g_n_sm = 1;
+    }
+    const int per_member = std::max(1, g_n_sm / nb);
+    long rpc = (rows + per_member - 1) / per_member;
+    rpc = (rpc + WG_ROWS - 1) / WG_ROWS * WG_ROWS;
+    const int nx = (int)((rows + rpc - 1) / rpc);
+    k_wgrad_tc05<<<dim3(nx, nb), WG_THREADS, WG_SMEM, st>>>(X, x_ms, Kd, D, d_ms, Nd, rows, rpc, G, g_ms, err);
+}
+
 
 // ---------------------------------------------------------------------------
 // elementwise kernels
@@ -1097,12 +1291,17 @@ void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, 
     const long dms[4] = {ys, ys, ys, s->os};
     float *grad = s->grad_all + (size_t)k0 * NPAR;
     for (int l = 0; l < 4; l++) {
-        Epi w{};
-        w.s_out = grad + WOFF[l];
-        w.s_ld = NDIM[l];
-        w.ms_out = NPAR;
-        gemm<EPI_WGRAD, true>(s->stream, Ain[l], KDIM[l], dOut[l], NDIM[l], KDIM[l], NDIM[l], (int)rows, w, split, nk,
-                              ams[l], dms[l]);
+        if (tc) {
+            wgrad_tc05(s->stream, Ain[l], ams[l], KDIM[l], dOut[l], dms[l], NDIM[l], rows, grad + WOFF[l], NPAR, nk,
+                       s->d_err);
+        } else {
+            Epi w{};
+            w.s_out = grad + WOFF[l];
+            w.s_ld = NDIM[l];
+            w.ms_out = NPAR;
+            gemm<EPI_WGRAD, true>(s->stream, Ain[l], KDIM[l], dOut[l], NDIM[l], KDIM[l], NDIM[l], (int)rows, w, split,
+                                  nk, ams[l], dms[l]);
+        }
         dim3 g(cdiv(NDIM[l], 128), cdiv(rows, 2048), nk);
         k_colsum<<<g, 128, 0, s->stream>>>(dOut[l], rows, NDIM[l], grad + BOFF[l], dms[l], NPAR);
     }
