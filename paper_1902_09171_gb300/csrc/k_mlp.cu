@@ -239,7 +239,8 @@ void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *
 // ---------------------------------------------------------------------------
 // The same GEMM on the 5th-generation tensor cores (tcgen05): C[M x N] =
 // A[M x K] * Bk[N x K]^T with both operands K-major.  One CTA computes a
-// 128 x 64 tile with the whole K (<= 256) resident in shared memory:
+// 128 x 256 tile (every output column of this network: the A rows are read
+// once) with the whole K (<= 256) resident in shared memory:
 //   * operands are copied (cp.async, 16 bytes per copy) into shared memory in
 //     the K-major "core matrix" layout (8 rows x 16 bytes per core matrix, no
 //     swizzle): core (r/8, k/8) at byte (k/8 * rows/8 + r/8) * 128, row r%8 at
@@ -247,10 +248,11 @@ void gemm(cudaStream_t s, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *
 //   * one elected thread issues K/16 tcgen05.mma (kind::f16, BF16 inputs,
 //     FP32 accumulator in tensor memory) and a tcgen05.commit onto an mbarrier;
 //   * every warp waits on the mbarrier (bounded), reads its 32 accumulator rows
-//     with tcgen05.ld and runs the fused epilogue sixteen columns at a time
-//     with 16-byte stores; tensor memory is freed on every path.
+//     (its lane quarter) of one 64-column part with tcgen05.ld and runs the
+//     fused epilogue sixteen columns at a time with 16-byte stores (sixteen
+//     warps); tensor memory is freed on every path.
 // ---------------------------------------------------------------------------
-constexpr int TC_M = 128, TC_N = 64, TC_THREADS = 128, TC_SPIN = 1 << 22;
+constexpr int TC_M = 128, TC_N = 256, TC_THREADS = 512, TC_SPIN = 1 << 22;
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *_
     epi_member(e, blockIdx.z);
     const int KC = K >> 3;  // 16-byte chunks along K
     unsigned char *sA = tc_smem, *sB = tc_smem + (size_t)TC_M * K * 2;
-    // tensor memory: 64 columns x 128 lanes of FP32 for the 128 x 64 accumulator
+    // tensor memory: 256 columns x 128 lanes of FP32 for the 128 x 256 accumulator
     if (warp == 0) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(TC_N)
@@ -343,11 +345,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc05(const __nv_bfloat16 *_
     const int ok = __syncthreads_and(done);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int row = m0 + warp * 32 + lane;
+        // warp w: accumulator rows 32 (w % 4) .. (its lane quarter), columns 64 (w / 4) ..
+        const int quarter = warp & 3, part = warp >> 2;
+        const int row = m0 + quarter * 32 + lane;
 #pragma unroll
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        for (int c0 = part * 64; c0 < part * 64 + 64; c0 += 16) {
+            if (n0 + c0 >= N) break;
             unsigned r[16];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                 "[%16];\n"
@@ -969,36 +974,56 @@ __global__ void k_build_input(const float *__restrict__ U, int B, int T, int t, 
 
 // head gradient do_t = [scale (s - y/s_scale), dh (1 - h^2), 0]; loss partials
 // Member blockIdx.y of a member-batched launch: S, Hrow, dZ and dO advance by
-// their member strides, loss_acc by one.
+// their member strides.
 __global__ void k_head_grad(const float *__restrict__ S, long s_ms, const float *__restrict__ Y, int B, int T, int t,
                             const float *__restrict__ s_inv, const __nv_bfloat16 *__restrict__ Hrow, long h_ms,
                             const float *__restrict__ dZ, long dz_ms, int have_dh, float gscale, __nv_bfloat16 *dO,
-                            long do_ms, double *loss_acc) {
+                            long do_ms) {
     const int z = blockIdx.y;
     S += z * s_ms;
     Hrow += z * h_ms;
     dZ += z * dz_ms;
     dO += z * do_ms;
-    loss_acc += z;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.0f;
-    if (idx < B * N4) {
-        const int b = idx / N4, n = idx % N4;
-        float v = 0.0f;
-        if (n < NOUT) {
-            const float r = S[((size_t)b * T + t) * NOUT + n] - Y[((size_t)b * T + t) * NOUT + n] * s_inv[n];
-            v = gscale * r;
-            l = r * r;
-        } else if (n < NOUT + NH && have_dh) {
-            const float h = __bfloat162float(Hrow[(size_t)b * K0 + NIN + (n - NOUT)]);
-            v = dZ[(size_t)b * K0 + NIN + (n - NOUT)] * (1.0f - h * h);
-        }
-        dO[idx] = __float2bfloat16(v);
+    if (idx >= B * N4) return;
+    const int b = idx / N4, n = idx % N4;
+    float v = 0.0f;
+    if (n < NOUT) {
+        v = gscale * (S[((size_t)b * T + t) * NOUT + n] - Y[((size_t)b * T + t) * NOUT + n] * s_inv[n]);
+    } else if (n < NOUT + NH && have_dh) {
+        const float h = __bfloat162float(Hrow[(size_t)b * K0 + NIN + (n - NOUT)]);
+        v = dZ[(size_t)b * K0 + NIN + (n - NOUT)] * (1.0f - h * h);
     }
-    // loss partial sums
+    dO[idx] = __float2bfloat16(v);
+}
+
+// loss partial sums sum (s - y / s_scale)^2 over the n stress values of member
+// blockIdx.y (S at + y s_ms), one FP64 atomic per block into loss_acc[y]
+constexpr int LOSS_THREADS = 256, LOSS_PER_THREAD = 16;
+__global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float *__restrict__ S, long s_ms,
+                                                       const float *__restrict__ Y, long n,
+                                                       const float *__restrict__ s_inv, double *loss_acc) {
+    __shared__ double s_part[LOSS_THREADS / 32];
+    S += blockIdx.y * s_ms;
+    const long i0 = (long)blockIdx.x * LOSS_THREADS * LOSS_PER_THREAD + threadIdx.x;
+    double l = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < LOSS_PER_THREAD; k++) {
+        const long i = i0 + (long)k * LOSS_THREADS;
+        if (i < n) {
+            const float r = S[i] - Y[i] * s_inv[i % NOUT];
+            l += (double)(r * r);
+        }
+    }
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) l += __shfl_xor_sync(0xffffffffu, l, d);
-    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss_acc, (double)l);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < LOSS_THREADS / 32; w++) t += s_part[w];
+        atomicAdd(loss_acc + blockIdx.y, t);
+    }
 }
 
 // column sums of a [rows x N] bf16 matrix into g (FP32, accumulate); member
@@ -1246,12 +1271,16 @@ void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, 
         Wt[l] = s->Wt_all[l] + k0 * wms[l];
     }
     const bool tc = s->backend != 0;
+    {
+        const long n = (long)B * T * NOUT;
+        k_loss<<<dim3(cdiv(n, LOSS_THREADS * LOSS_PER_THREAD), nk), LOSS_THREADS, 0, s->stream>>>(S, s_ms, Y, n, s->s_inv,
+                                                                                               s->loss_acc + k0);
+    }
     for (int t = T - 1; t >= 0; t--) {
         __nv_bfloat16 *dOt = dO + (size_t)t * RB * N4;
         const __nv_bfloat16 *Hrow = (t + 1 < T) ? Z + (size_t)(t + 1) * RB * K0 : Z;
         k_head_grad<<<dim3(cdiv(RB * N4, 256), nk), 256, 0, s->stream>>>(S, s_ms, Y, B, T, t, s->s_inv, Hrow, s->zs,
-                                                                         dZ, s->dzs, t + 1 < T, gscale, dOt, s->os,
-                                                                         s->loss_acc + k0);
+                                                                         dZ, s->dzs, t + 1 < T, gscale, dOt, s->os);
         Epi e{};
         e.ld_out = WID;
         e.ld_in = WID;
