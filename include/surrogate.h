@@ -82,12 +82,13 @@ int sur_step(sur_ctx *s, const float *u, int n, float *h, float s_floor, float *
  * `stream`. */
 int sur_features(const double *F_prev, const double *F, int n, float *u, void *stream);
 
-/* Tensor-core engine: 2 = the whole recurrent forward (all layers, all steps)
- * in one 5th-generation tensor-core (tcgen05) kernel per 128-row tile, with
- * the activations on chip, and one tcgen05 GEMM per layer and step for the
- * data gradients (the default); 1 = one tcgen05 GEMM per layer and step for
- * both; 0 = warp-level BF16 instructions (mma.sync) for both.  Weight
- * gradients always use mma.sync.  Same results up to summation order.
+/* Tensor-core engine: 2 = the whole recurrent forward and the whole BPTT
+ * data-gradient chain (all layers, all steps) each in one 5th-generation
+ * tensor-core (tcgen05) kernel per 128-row tile, with the operands on chip,
+ * and the members trained side by side (the default); 1 = one tcgen05 GEMM
+ * per layer and step; 0 = warp-level BF16 instructions (mma.sync).  Weight
+ * gradients use a tcgen05 kernel for engines 1 and 2, mma.sync for 0.  Same
+ * results up to summation order and the rounding of the GELU' evaluation.
  * RC_EINVAL for another value. */
 int sur_set_backend(sur_ctx *s, int backend);
 

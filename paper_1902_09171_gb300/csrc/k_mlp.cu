@@ -633,6 +633,64 @@ __device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tzo, long t
     }
 }
 
+// The producer thread of the warp-specialised kernels: streams T x FT_CHUNKS
+// weight chunks (per step four layers of 4, 4, 4 and 3 chunks of 64 rows; K =
+// K0 for the first layer, WID for the others) through the FT_NBUF buffers and
+// issues each layer's MMAs (A operand in sZA, accumulator columns 64 q ..) as
+// soon as the epilogue warps have handed the operand over.  False on a timeout.
+__device__ __forceinline__ bool ws_produce(const unsigned char *Wp, int T, unsigned char *sZA, unsigned char *sW,
+                                           unsigned tmem, unsigned bar_full, unsigned bar_empty, unsigned bar_acc,
+                                           unsigned bar_epi) {
+    bool ok = true;
+    const long n_chunks = (long)T * FT_CHUNKS;
+    for (long c0 = 0; c0 < FT_NBUF && c0 < n_chunks; c0++) ws_bulk(sW, Wp, c0, bar_full);
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
+                           ((unsigned)(FT_M >> 4) << 24);
+    const unsigned aBase = (unsigned)__cvta_generic_to_shared(sZA);
+    const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
+    long c = 0;
+    for (int t = 0; t < T && ok; t++)
+        for (int l = 0; l < 4 && ok; l++) {
+            // the layer's operand is in place and the accumulator has been read
+            ok = ws_wait(bar_epi, (unsigned)((t * 4 + l) & 1));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int Kl = l == 0 ? K0 : WID, nq = l == 3 ? 3 : 4;
+            for (int q = 0; q < nq; q++, c++) {
+                const int b = (int)(c % FT_NBUF);
+                ok = ws_wait(bar_full + 8u * b, (unsigned)((c / FT_NBUF) & 1));
+                if (!ok) break;
+                const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + (size_t)b * FT_SW);
+                const unsigned dcol = tmem + (unsigned)(q * FT_NC);
+                for (int kk = 0; kk < (Kl >> 4); kk++) {
+                    const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
+                    const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
+                    const unsigned acc = kk > 0;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 bar_empty + 8u * b)
+                             : "memory");
+                // refill the buffer of chunk c - 1 once the MMAs that read it are done
+                if (c >= 1 && c - 1 + FT_NBUF < n_chunks) {
+                    const int pb = (int)((c - 1) % FT_NBUF);
+                    ok = ws_wait(bar_empty + 8u * pb, (unsigned)(((c - 1) / FT_NBUF) & 1));
+                    if (!ok) break;
+                    ws_bulk(sW, Wp, c - 1 + FT_NBUF, bar_full);
+                }
+            }
+            if (!ok) break;
+            // the accumulator is complete once every MMA issued so far is
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_acc)
+                         : "memory");
+        }
+    return ok;
+}
+
 __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     extern __shared__ __align__(1024) unsigned char ft_smem[];
     __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi;
@@ -679,55 +737,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     if (warp == WS_EPI_WARPS) {
         // ---- producer: weight chunks and MMAs (one thread) ----
         if (lane == 0) {
-            const unsigned char *Wp = a.Wp[mk];
-            const long n_chunks = (long)T * FT_CHUNKS;
-            for (long c0 = 0; c0 < FT_NBUF && c0 < n_chunks; c0++) ws_bulk(sW, Wp, c0, bar_full);
-            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
-                                   ((unsigned)(FT_M >> 4) << 24);
-            const unsigned aBase = (unsigned)__cvta_generic_to_shared(sZA);
-            const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
-            long c = 0;
-            for (int t = 0; t < T && ok; t++)
-                for (int l = 0; l < 4 && ok; l++) {
-                    // the layer's operand is in place and the accumulator has been read
-                    ok = ws_wait(bar_epi, (unsigned)((t * 4 + l) & 1));
-                    if (!ok) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int Kl = l == 0 ? K0 : WID, nq = l == 3 ? 3 : 4;
-                    for (int q = 0; q < nq; q++, c++) {
-                        const int b = (int)(c % FT_NBUF);
-                        ok = ws_wait(bar_full + 8u * b, (unsigned)((c / FT_NBUF) & 1));
-                        if (!ok) break;
-                        const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + (size_t)b * FT_SW);
-                        const unsigned dcol = tmem + (unsigned)(q * FT_NC);
-                        for (int kk = 0; kk < (Kl >> 4); kk++) {
-                            const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
-                            const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
-                            const unsigned acc = kk > 0;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                                : "memory");
-                        }
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                bar_empty + 8u * b)
-                            : "memory");
-                        // refill the buffer of chunk c - 1 once the MMAs that read it are done
-                        if (c >= 1 && c - 1 + FT_NBUF < n_chunks) {
-                            const int pb = (int)((c - 1) % FT_NBUF);
-                            ok = ws_wait(bar_empty + 8u * pb, (unsigned)(((c - 1) / FT_NBUF) & 1));
-                            if (!ok) break;
-                            ws_bulk(sW, Wp, c - 1 + FT_NBUF, bar_full);
-                        }
-                    }
-                    if (!ok) break;
-                    // the accumulator is complete once every MMA issued so far is
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     bar_acc)
-                                 : "memory");
-                }
+            ok = ws_produce(a.Wp[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi);
             if (!ok) atomicExch(a.err, RC_ETIMEOUT);
         }
     } else {
@@ -933,8 +943,219 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The whole BPTT data-gradient chain in one kernel (tcgen05), the mirror of
+// k_forward_ws: a CTA owns 128 rows of one member and walks the steps
+// t = T-1 .. 0; per step the four products
+//   dY3 = (dO_t W4^T) * gelu'(Y3_t),  dY2 = (dY3 W3^T) * gelu'(Y2_t),
+//   dY1 = (dY2 W2^T) * gelu'(Y1_t),   dZ_t = dY1 W1^T
+// run back to back on the tensor cores with the operand in shared memory and
+// the accumulator in tensor memory.  They have the forward's shapes in the
+// reverse order, so the same producer streams the members' backward weight
+// images (W4, W3, W2, W1 packed by k_pack_weights as the forward packs W1^T ..
+// W4^T).  The epilogue warps read Y_l from the tape, write dY_l into shared
+// memory (the next operand) and to global memory (for the weight gradients);
+// after dZ_t they build dO_{t-1} = [gscale (s - y / s_scale), dZ_t(state) *
+// (1 - h_{t-1}^2), 0] from the predictions, the targets and the state row of
+// the tape.  GELU' uses the Abramowitz & Stegun 7.1.26 erf of the forward,
+// whose exp(-x^2/2) is also the Gaussian density term.
+// ---------------------------------------------------------------------------
+struct BwdArgs {
+    int B, T;
+    const float *S;  // predictions in network units: member k, row b, step t at S + k s_mstride + (b T + t) NOUT
+    long s_mstride;
+    const float *Y;  // targets, (b T + t) NOUT
+    const float *s_inv;
+    float gscale;
+    const __nv_bfloat16 *Z, *Yt[3];  // tape of the launch's first member: Z rows (t B + b) K0, Y1..Y3 rows WID
+    __nv_bfloat16 *dO, *dY[3];       // outputs, rows (t B + b): dO N4 wide, dY1..dY3 WID wide
+    long z_ms, y_ms, o_ms;           // member strides (elements)
+    const unsigned char *Wb[FT_MAXK];
+    int *err;
+};
+
+__device__ __forceinline__ float gelu_grad_as(float x) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = __expf(-z * z);  // exp(-x^2 / 2)
+    const float erf_abs = 1.0f - poly * e;
+    return 0.5f * (1.0f + copysignf(erf_abs, x)) + x * e * 0.3989422804014327f;
+}
+
+// dO of step tp = t - 1 (or T - 1 at the start, with no state part): stress
+// columns and zero padding of row `row` (the state columns come from dZ)
+__device__ __forceinline__ float wb_stress_grad(const BwdArgs &a, const float *S, int b, int tp, int n) {
+    const size_t i = ((size_t)b * a.T + tp) * NOUT + n;
+    return a.gscale * (S[i] - a.Y[i] * a.s_inv[n]);
+}
+
+__device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, long oo, int l, int t, int quarter,
+                                            int part, int lane, unsigned tmem, unsigned char *sZA, const float *S,
+                                            int m0) {
+    const int B = a.B, row = quarter * 32 + lane, b = m0 + row;
+    const bool live = b < B;
+    if (l < 3) {  // dY_{3-l} = acc * gelu'(Y_{3-l})
+        const __nv_bfloat16 *Yg = a.Yt[2 - l] + yo + ((size_t)t * B + b) * WID;
+        __nv_bfloat16 *dY = a.dY[2 - l] + yo + ((size_t)t * B + b) * WID;
+        const int nch = WID >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
+        for (int ch = ch0; ch < ch1; ch++) {
+            const int n0 = ch * 16;
+            unsigned r[16];
+            const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            uint4 y0 = make_uint4(0u, 0u, 0u, 0u), y1 = y0;
+            if (live) {
+                y0 = reinterpret_cast<const uint4 *>(Yg + n0)[0];
+                y1 = reinterpret_cast<const uint4 *>(Yg + n0)[1];
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const unsigned yw[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+            unsigned dp[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const __nv_bfloat162 yy = *reinterpret_cast<const __nv_bfloat162 *>(&yw[j]);
+                const float g0 = __uint_as_float(r[2 * j]) * gelu_grad_as(__low2float(yy));
+                const float g1 = __uint_as_float(r[2 * j + 1]) * gelu_grad_as(__high2float(yy));
+                dp[j] = bf16x2_bits(g0, g1);
+            }
+            const uint4 d0 = make_uint4(dp[0], dp[1], dp[2], dp[3]), d1 = make_uint4(dp[4], dp[5], dp[6], dp[7]);
+            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = d0;
+            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = d1;
+            if (live) {
+                reinterpret_cast<uint4 *>(dY + n0)[0] = d0;
+                reinterpret_cast<uint4 *>(dY + n0)[1] = d1;
+            }
+        }
+        return;
+    }
+    // dZ_t -> dO_{t-1}; nothing to hand on after step 0
+    if (t == 0) return;
+    const int tp = t - 1;
+    const __nv_bfloat16 *Zt = a.Z + zo + ((size_t)t * B + b) * K0;  // [u_t, h_{t-1}, 0]
+    __nv_bfloat16 *dOp = a.dO + oo + ((size_t)tp * B + b) * N4;
+    const int nch = N4 >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
+    for (int ch = ch0; ch < ch1; ch++) {
+        const int n0 = ch * 16;
+        unsigned r[16];
+        const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int n = n0 + j;
+            if (n >= NIN && n < NIN + NH) {
+                const float h = live ? __bfloat162float(Zt[n]) : 0.0f;
+                const unsigned short hb = bf16_bits(__uint_as_float(r[j]) * (1.0f - h * h));
+                *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NOUT + n - NIN, FT_M)) = hb;
+                if (live) reinterpret_cast<unsigned short *>(dOp)[NOUT + n - NIN] = hb;
+            }
+        }
+    }
+    if (part == 0) {  // the stress columns and the padding of dO_{t-1}
+        for (int n = 0; n < NOUT; n++) {
+            const unsigned short v = bf16_bits(live ? wb_stress_grad(a, S, b, tp, n) : 0.0f);
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = v;
+            if (live) reinterpret_cast<unsigned short *>(dOp)[n] = v;
+        }
+        for (int n = NOUT + NH; n < K0; n++) {
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = 0;
+            if (live) reinterpret_cast<unsigned short *>(dOp)[n] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
+    extern __shared__ __align__(1024) unsigned char ft_smem[];
+    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi;
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
+    const long zo = mk * a.z_ms, yo = mk * a.y_ms, oo = mk * a.o_ms;
+    unsigned char *sZA = ft_smem, *sW = ft_smem + FT_SA;
+    const float *S = a.S + mk * a.s_mstride;
+    const int T = a.T;
+
+    if (warp == 0) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(WID)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const unsigned bar_full = (unsigned)__cvta_generic_to_shared(&s_full[0]);
+    const unsigned bar_empty = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
+    const unsigned bar_acc = (unsigned)__cvta_generic_to_shared(&s_acc);
+    const unsigned bar_epi = (unsigned)__cvta_generic_to_shared(&s_epi);
+    if (tid == 0) {
+        for (int i = 0; i < FT_NBUF; i++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full + 8 * i) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_empty + 8 * i) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_acc) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_epi), "r"(WS_EPI_WARPS) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    bool ok = true;
+
+    if (warp == WS_EPI_WARPS) {
+        if (lane == 0) {
+            ok = ws_produce(a.Wb[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi);
+            if (!ok) atomicExch(a.err, RC_ETIMEOUT);
+        }
+    } else {
+        const int etid = tid, nthr = WS_EPI_WARPS * 32, quarter = warp & 3, part = warp >> 2;
+        // dO_{T-1}: stress columns only
+        for (int idx = etid; idx < FT_M * K0; idx += nthr) {
+            const int r = idx / K0, n = idx - r * K0, b = m0 + r;
+            const float v = (n < NOUT && b < a.B) ? wb_stress_grad(a, S, b, T - 1, n) : 0.0f;
+            const unsigned short hv = bf16_bits(v);
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(r, n, FT_M)) = hv;
+            if (b < a.B) reinterpret_cast<unsigned short *>(a.dO + oo)[((size_t)(T - 1) * a.B + b) * N4 + n] = hv;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+        for (int i = 0; i < T && ok; i++)
+            for (int l = 0; l < 4 && ok; l++) {
+                ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((i * 4 + l) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                wb_epilogue(a, zo, yo, oo, l, T - 1 - i, quarter, part, lane, tmem, sZA, S, m0);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+            }
+        if (!ok && lane == 0) atomicExch(a.err, RC_ETIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WID) : "memory");
+    }
+}
+
 void prepare_ws() {
     cudaFuncSetAttribute(k_forward_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
+    cudaFuncSetAttribute(k_backward_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
     cudaFuncSetAttribute(k_wgrad_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
 }
 
@@ -1122,6 +1343,7 @@ struct SurMember {
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16 *W[4] = {nullptr}, *Wt[4] = {nullptr};
     unsigned char *Wp = nullptr;  // weight chunks in the layout of the fused forward's shared buffers
+    unsigned char *Wb = nullptr;  // the same for the fused backward (W4, W3, W2, W1)
     int step = 0;
 };
 
@@ -1147,7 +1369,7 @@ struct sur_ctx {
     // parameters of all members, member after member (the SurMember pointers point into these)
     float *theta_all = nullptr, *grad_all = nullptr, *m_all = nullptr, *v_all = nullptr;
     __nv_bfloat16 *W_all[4] = {nullptr}, *Wt_all[4] = {nullptr};
-    unsigned char *Wp_all = nullptr;
+    unsigned char *Wp_all = nullptr, *Wb_all = nullptr;
 };
 
 namespace {
@@ -1170,6 +1392,9 @@ void cast_member(sur_ctx *s, SurMember &M) {
                                                                                   KDIM[l], NDIM[l]);
     const int units = WS_WP_BYTES / 16;
     k_pack_weights<<<cdiv(units, 256), 256, 0, s->stream>>>(M.Wt[0], M.Wt[1], M.Wt[2], M.Wt[3], M.Wp);
+    // the backward products use W4 [256 x 144], W3, W2 and W1 [144 x 256] as the
+    // forward uses W1^T [256 x 144], W2^T, W3^T and W4^T [144 x 256]
+    k_pack_weights<<<cdiv(units, 256), 256, 0, s->stream>>>(M.W[3], M.W[2], M.W[1], M.W[0], M.Wb);
 }
 
 // forward through T steps for member M; stress predictions into S (B x T x 6)
@@ -1276,7 +1501,34 @@ void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, 
         k_loss<<<dim3(cdiv(n, LOSS_THREADS * LOSS_PER_THREAD), nk), LOSS_THREADS, 0, s->stream>>>(S, s_ms, Y, n, s->s_inv,
                                                                                                s->loss_acc + k0);
     }
-    for (int t = T - 1; t >= 0; t--) {
+    if (s->backend == 2) {  // the whole data-gradient chain in one kernel per FT_MAXK members
+        for (int g = 0; g < nk; g += FT_MAXK) {
+            const int ng = std::min(FT_MAXK, nk - g);
+            BwdArgs ba{};
+            ba.B = B;
+            ba.T = T;
+            ba.S = S + g * s_ms;
+            ba.s_mstride = s_ms;
+            ba.Y = Y;
+            ba.s_inv = s->s_inv;
+            ba.gscale = gscale;
+            ba.Z = Z + g * s->zs;
+            ba.Yt[0] = Y1 + g * ys;
+            ba.Yt[1] = Y2 + g * ys;
+            ba.Yt[2] = Y3 + g * ys;
+            ba.dO = dO + g * s->os;
+            ba.dY[0] = dY1 + g * ys;
+            ba.dY[1] = dY2 + g * ys;
+            ba.dY[2] = dY3 + g * ys;
+            ba.z_ms = s->zs;
+            ba.y_ms = ys;
+            ba.o_ms = s->os;
+            for (int i = 0; i < ng; i++) ba.Wb[i] = s->mem[k0 + g + i].Wb;
+            ba.err = s->d_err;
+            k_backward_ws<<<dim3(cdiv(B, FT_M), ng), WS_THREADS, FT_SMEM, s->stream>>>(ba);
+        }
+    }
+    for (int t = T - 1; t >= 0 && s->backend != 2; t--) {
         __nv_bfloat16 *dOt = dO + (size_t)t * RB * N4;
         const __nv_bfloat16 *Hrow = (t + 1 < T) ? Z + (size_t)(t + 1) * RB * K0 : Z;
         k_head_grad<<<dim3(cdiv(RB * N4, 256), nk), 256, 0, s->stream>>>(S, s_ms, Y, B, T, t, s->s_inv, Hrow, s->zs,
@@ -1409,6 +1661,7 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
         ok &= salloc(s, &s->Wt_all[l], Kn * KDIM[l] * NDIM[l]) == cudaSuccess;
     }
     ok &= salloc(s, &s->Wp_all, Kn * WS_WP_BYTES) == cudaSuccess;
+    ok &= salloc(s, &s->Wb_all, Kn * WS_WP_BYTES) == cudaSuccess;
     if (!ok) { sur_destroy(s); return RC_ENOMEM; }
     prepare_tc05();
     prepare_ws();
@@ -1424,6 +1677,7 @@ int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void 
             M.Wt[l] = s->Wt_all[l] + k * KDIM[l] * NDIM[l];
         }
         M.Wp = s->Wp_all + k * WS_WP_BYTES;
+        M.Wb = s->Wb_all + k * WS_WP_BYTES;
     }
     float one[NIN];
     for (int k = 0; k < NIN; k++) one[k] = 1.0f;

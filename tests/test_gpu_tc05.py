@@ -2,8 +2,9 @@
 accumulator in tensor memory) against the FP64 oracle and against the
 mma.sync path, on ragged batch sizes:
   backend 1: one tcgen05 GEMM per layer and step;
-  backend 2: the whole recurrent forward in one kernel per 128-row tile
-             (weights streamed through shared memory, activations on chip)."""
+  backend 2: the whole recurrent forward and the whole BPTT data-gradient
+             chain each in one kernel per 128-row tile (weights streamed
+             through shared memory, operands on chip), members side by side."""
 import numpy as np
 import pytest
 
@@ -129,3 +130,33 @@ def test_fused_step_carries_state_like_the_layerwise_step(torch):
     assert np.abs(res[2][0] - res[0][0]).max() <= 5e-2 * scale
     assert np.abs(res[2][2] - res[0][2]).max() <= 5e-2
     assert np.all(np.isfinite(res[2][1])) and np.abs(res[2][1] - res[0][1]).max() <= 0.1 * max(res[0][1].max(), 1e-3)
+
+
+def test_member_batched_training_step_matches_oracle(torch):
+    # sur_train_step on the default engine: the fused forward and the fused BPTT
+    # kernel over three members at once, two row tiles with a ragged tail, 12
+    # steps.  Each member's loss against the oracle, and its first AdamW update,
+    # which for lr >> eps moves every parameter by about -lr sign(gradient)
+    # (weight decay off), against the signs of the oracle gradient.
+    B, T, K, lr = 150, 12, 3, 1e-3
+    thetas = [problem(70 + k, B, T)[0] for k in range(K)]
+    _, U, Y = problem(80, B, T)
+    s = S.sur_create(K, B, T, 0)
+    try:
+        for k in range(K):
+            S.sur_set_params(s, k, thetas[k])
+        dU = torch.tensor(U, dtype=torch.float32, device="cuda")
+        dY = torch.tensor(Y, dtype=torch.float32, device="cuda")
+        loss = S.sur_train_step(s, dU, dY, lr, wd=0.0, n_members=K)
+        assert S.sur_sync(s) == 0
+        after = [S.sur_get_params(s, k) for k in range(K)]
+    finally:
+        S.sur_destroy(s)
+    for k in range(K):
+        Lr, gr = mlp.loss_and_grad(bf16_weights(thetas[k].astype(np.float64)), bf16(U), Y)
+        assert abs(loss[k] - Lr) <= 2e-2 * Lr, (k, loss[k], Lr)
+        step = after[k].astype(np.float64) - thetas[k].astype(np.float64)
+        big = np.abs(gr) > 1e-2 * np.abs(gr).max()
+        agree = np.mean(np.sign(step[big]) == -np.sign(gr[big]))
+        assert agree > 0.99, (k, agree)
+        assert np.abs(step[big]).max() <= 1.01 * lr
