@@ -469,6 +469,19 @@ __device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
     return *reinterpret_cast<const unsigned *>(&p);
 }
 
+// 32-byte global store / read-only load of 16 BF16 values (one whole sector per
+// lane); the address must be 32-byte aligned
+__device__ __forceinline__ void st_v8(void *p, const uint4 &lo, const uint4 &hi) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(lo.x), "r"(lo.y),
+                 "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_v8(const void *p, uint4 &lo, uint4 &hi) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+                 : "l"(p));
+}
+
 // GELU x/2 (1 + erf(x / sqrt 2)) with erf from the rational approximation of
 // Abramowitz & Stegun, Handbook of Mathematical Functions (1964), formula
 // 7.1.26 (|error| <= 1.5e-7 for x >= 0; odd extension), far below the BF16
@@ -606,12 +619,9 @@ __device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tzo, long t
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = a1;
             if (tape && b < B) {
-                uint4 *py = reinterpret_cast<uint4 *>(a.tY[l] + tyo + ((size_t)t * B + b) * WID + n0);
-                uint4 *pa = reinterpret_cast<uint4 *>(a.tA[l] + tyo + ((size_t)t * B + b) * WID + n0);
-                py[0] = make_uint4(yp[0], yp[1], yp[2], yp[3]);
-                py[1] = make_uint4(yp[4], yp[5], yp[6], yp[7]);
-                pa[0] = a0;
-                pa[1] = a1;
+                st_v8(a.tY[l] + tyo + ((size_t)t * B + b) * WID + n0, make_uint4(yp[0], yp[1], yp[2], yp[3]),
+                      make_uint4(yp[4], yp[5], yp[6], yp[7]));
+                st_v8(a.tA[l] + tyo + ((size_t)t * B + b) * WID + n0, a0, a1);
             }
         } else {
 #pragma unroll
@@ -785,8 +795,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
 // 256 FP32 columns each fill the 512 columns of tensor memory; a three-stage
 // pipeline of 64-row chunks (X 32 KB + D 32 KB per stage) keeps the copies of
 // the next chunks in flight while the MMAs of the current one run; the partial
-// sums are added into G (FP32 atomics).  Member blockIdx.y of a member-batched
-// launch reads X + y x_ms, D + y d_ms and adds into G + y g_ms.
+// sums are added into G (FP32 atomics).  With Gb, the column sums of D (the
+// bias gradient) are formed from the same staged chunks: lanes 8p .. 8p+7 read
+// the eight rows of one core matrix (128 contiguous bytes) and keep eight
+// running sums each.  Member blockIdx.y of a member-batched launch reads
+// X + y x_ms, D + y d_ms and adds into G + y g_ms, Gb + y g_ms.
 // ---------------------------------------------------------------------------
 constexpr int WG_ROWS = 64, WG_STAGES = 3, WG_THREADS = 128;
 constexpr int WG_SX = 256 * WG_ROWS * 2, WG_SD = 256 * WG_ROWS * 2, WG_STAGE = WG_SX + WG_SD;
@@ -794,7 +807,7 @@ constexpr int WG_SMEM = WG_STAGES * WG_STAGE;
 
 __global__ void __launch_bounds__(WG_THREADS, 1)
     k_wgrad_tc05(const __nv_bfloat16 *__restrict__ X, long x_ms, int Kd, const __nv_bfloat16 *__restrict__ D,
-                 long d_ms, int Nd, long rows, long rows_per_cta, float *G, long g_ms, int *err) {
+                 long d_ms, int Nd, long rows, long rows_per_cta, float *G, float *Gb, long g_ms, int *err) {
     extern __shared__ __align__(1024) unsigned char wg_smem[];
     __shared__ __align__(8) unsigned long long s_done[WG_STAGES];
     __shared__ unsigned s_tmem;
@@ -802,6 +815,12 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     X += blockIdx.y * x_ms;
     D += blockIdx.y * d_ms;
     G += blockIdx.y * g_ms;
+    if (Gb) Gb += blockIdx.y * g_ms;
+    float csum[2][8];  // column sums: pieces tid / 8 and tid / 8 + 16, row tid % 8 of each core matrix
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) csum[q][e] = 0.0f;
     const long r_begin = (long)blockIdx.x * rows_per_cta;
     const long r_end = r_begin + rows_per_cta < rows ? r_begin + rows_per_cta : rows;
     const int n_chunks = r_end > r_begin ? (int)((r_end - r_begin + WG_ROWS - 1) / WG_ROWS) : 0;
@@ -884,6 +903,25 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                          : "memory");
         }
         issued = c;
+        if (Gb) {  // this chunk's rows into the column sums (rows past the matrix are zero)
+            const unsigned char *sd = wg_smem + (size_t)(c % WG_STAGES) * WG_STAGE + WG_SX;
+            const int j = tid & 7, p = tid >> 3;
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int pc = p + 16 * q;
+                if (pc < DC)
+                    for (int rg = 0; rg < WG_ROWS / 8; rg++) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(sd + ((rg * DC + pc) * 128 + j * 16));
+                        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[e]);
+                            csum[q][2 * e] += __low2float(x2);
+                            csum[q][2 * e + 1] += __high2float(x2);
+                        }
+                    }
+            }
+        }
         // the stage of chunk c - 1 takes chunk c + STAGES - 1 once its MMAs are done
         const int cn = c + WG_STAGES - 1;
         if (cn < n_chunks) {
@@ -904,6 +942,20 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     }
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && n_chunks > 0 && Gb) {
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int pc = (tid >> 3) + 16 * q;
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                float v = csum[q][e];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                if ((tid & 7) == 0 && pc < DC) atomicAdd(&Gb[pc * 8 + e], v);
+            }
+        }
+    }
     if (ok && n_chunks > 0) {
         for (int h = 0; h < MH; h++) {
             const int m = h * 128 + warp * 32 + lane;
@@ -1012,10 +1064,7 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
                 : "r"(taddr)
                 : "memory");
             uint4 y0 = make_uint4(0u, 0u, 0u, 0u), y1 = y0;
-            if (live) {
-                y0 = reinterpret_cast<const uint4 *>(Yg + n0)[0];
-                y1 = reinterpret_cast<const uint4 *>(Yg + n0)[1];
-            }
+            if (live) ld_v8(Yg + n0, y0, y1);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const unsigned yw[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
             unsigned dp[8];
@@ -1029,10 +1078,7 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
             const uint4 d0 = make_uint4(dp[0], dp[1], dp[2], dp[3]), d1 = make_uint4(dp[4], dp[5], dp[6], dp[7]);
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = d0;
             *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = d1;
-            if (live) {
-                reinterpret_cast<uint4 *>(dY + n0)[0] = d0;
-                reinterpret_cast<uint4 *>(dY + n0)[1] = d1;
-            }
+            if (live) st_v8(dY + n0, d0, d1);
         }
         return;
     }
@@ -1164,7 +1210,7 @@ int g_n_sm = 0;
 // the weight gradients of nb members: G_i += X_i^T D_i over `rows` rows, about
 // one CTA per SM in all
 void wgrad_tc05(cudaStream_t st, const __nv_bfloat16 *X, long x_ms, int Kd, const __nv_bfloat16 *D, long d_ms, int Nd,
-                long rows, float *G, long g_ms, int nb, int *err) {
+                long rows, float *G, float *Gb, long g_ms, int nb, int *err) {
     if (g_n_sm <= 0) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1175,7 +1221,7 @@ void wgrad_tc05(cudaStream_t st, const __nv_bfloat16 *X, long x_ms, int Kd, cons
     long rpc = (rows + per_member - 1) / per_member;
     rpc = (rpc + WG_ROWS - 1) / WG_ROWS * WG_ROWS;
     const int nx = (int)((rows + rpc - 1) / rpc);
-    k_wgrad_tc05<<<dim3(nx, nb), WG_THREADS, WG_SMEM, st>>>(X, x_ms, Kd, D, d_ms, Nd, rows, rpc, G, g_ms, err);
+    k_wgrad_tc05<<<dim3(nx, nb), WG_THREADS, WG_SMEM, st>>>(X, x_ms, Kd, D, d_ms, Nd, rows, rpc, G, Gb, g_ms, err);
 }
 
 
@@ -1572,9 +1618,10 @@ void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, 
     const long dms[4] = {ys, ys, ys, s->os};
     float *grad = s->grad_all + (size_t)k0 * NPAR;
     for (int l = 0; l < 4; l++) {
-        if (tc) {
-            wgrad_tc05(s->stream, Ain[l], ams[l], KDIM[l], dOut[l], dms[l], NDIM[l], rows, grad + WOFF[l], NPAR, nk,
-                       s->d_err);
+        if (tc) {  // weights and biases in one pass
+            wgrad_tc05(s->stream, Ain[l], ams[l], KDIM[l], dOut[l], dms[l], NDIM[l], rows, grad + WOFF[l],
+                       grad + BOFF[l], NPAR, nk, s->d_err);
+            continue;
         } else {
             Epi w{};
             w.s_out = grad + WOFF[l];
