@@ -538,10 +538,11 @@ def run_kg_statics(args):
 def run_surrogate_train(args):
     """The learned surrogate's tensor-core kernels at the training shapes (4
     members, batch 4096, 60 increments, synthetic features and targets): one
-    bench step = one AdamW step of every member (whole-forward tcgen05 kernel
-    with the BPTT tape, tcgen05 data gradients, split-K weight gradients); then
-    the ensemble prediction of the same batch, whose kernel carries the tensor
-    roofline."""
+    bench step = one AdamW step of every member side by side (whole-forward
+    tcgen05 kernel with the BPTT tape, whole-backward tcgen05 kernel, tcgen05
+    weight and bias gradients).  The roofline is that of the slower of the two
+    fused kernels, timed by sur_profile_step; the ensemble prediction of the
+    same batch is timed beside it."""
     import torch
 
     from paper_1902_09171_gb300 import build, rcell
@@ -576,6 +577,7 @@ def run_surrogate_train(args):
     e1.record(st)
     torch.cuda.synchronize()
     ms_pred = e0.elapsed_time(e1) / n_pred
+    phases = [S.sur_profile_step(s, U, Y) for _ in range(3)][-1]
     err = S.sur_sync(s)
     S.sur_destroy(s)
     flop_fwd = 2.0 * B * T * (144 * 256 + 2 * 256 * 256 + 256 * 144) * K
@@ -584,16 +586,22 @@ def run_surrogate_train(args):
         peak, peak_src = float(peaks["bf16_tflops"]), "measured bf16 burst (MEASURED_PEAKS.json)"
     except (OSError, ValueError, KeyError):
         peak, peak_src = 1900.0, "fallback: 1.9 PFLOP/s bf16 burst of an earlier GB300 measurement"
-    achieved = flop_fwd / (ms_pred / 1e3) / 1e12
+    # both fused kernels run the four products of every step of every member:
+    # the forward's FLOPs (the backward skips nothing but dZ of step 0)
+    dom = "backward" if phases["backward"] >= phases["forward_tape"] else "forward_tape"
+    achieved = flop_fwd / (phases[dom] / 1e3) / 1e12
     return {"metric": "surrogate training throughput (sequence-increments/s, 4-member ensemble)",
             "value": B * T * K / (ms / 1e3), "unit": "sequence-increments/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "status": err, "data": "synthetic",
             "dtype": "bf16 operands, f32 accumulation / master weights",
             "config": {"workload": "surrogate_train_4x4096x60", "members": K, "batch": B, "increments": T},
             "train_tflops": 3 * flop_fwd / (ms / 1e3) / 1e12,
-            "predict_ms": ms_pred,
+            "predict_ms": ms_pred, "predict_tflops": round(flop_fwd / (ms_pred / 1e3) / 1e12, 2),
+            "phase_ms": {k: round(v, 4) for k, v in phases.items()},
             "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_forward_ws (prediction)",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_backward_ws (BPTT data gradients)" if dom == "backward"
+                         else "k_forward_ws (forward with the BPTT tape)",
                          "peak_source": peak_src}}
 
 

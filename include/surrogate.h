@@ -67,6 +67,14 @@ int sur_train_step(sur_ctx *s, const float *U, const float *Y, int B, int T, flo
 /* Predict whole sequences: S (device) n_members x B x T x 6, raw units. */
 int sur_predict(sur_ctx *s, const float *U, int B, int T, float *S);
 
+/* Time the phases of one training step of every member without applying it
+ * (the parameters and optimiser state are unchanged; the gradient buffers are
+ * overwritten): ms_out[0] the forward with the BPTT tape, ms_out[1] the data
+ * gradients (the backward through time, with the loss), ms_out[2] the weight
+ * and bias gradients, from CUDA events on the context's stream.  U, Y device
+ * arrays as for sur_train_step.  Synchronises.  RC_EINVAL on a bad size. */
+int sur_profile_step(sur_ctx *s, const float *U, const float *Y, int B, int T, double *ms_out);
+
 /* One increment for n independent quadrature points and every member:
  *   u       device, n x 15 raw features of this increment
  *   h       device, n_members x n x 128 FP32 recurrent state (read, then

@@ -1524,7 +1524,8 @@ void forward(sur_ctx *s, int k, const float *U, int B, int T, float *S, const fl
 // BPTT for members k0 .. k0 + nk - 1 at once (their tape slices; predictions S
 // of member k0 + i at S + i s_ms): gradients into their grad blocks (zeroed
 // here), loss partial sums into loss_acc[k0 + i]
-void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, const float *S, long s_ms) {
+void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, const float *S, long s_ms,
+                      cudaEvent_t mid = nullptr) {
     const size_t RB = (size_t)B;
     cudaMemsetAsync(s->grad_all + (size_t)k0 * NPAR, 0, sizeof(float) * NPAR * nk, s->stream);
     const float gscale = 2.0f / ((float)B * T * NOUT);
@@ -1609,6 +1610,7 @@ void backward_members(sur_ctx *s, int k0, int nk, const float *Y, int B, int T, 
             else gemm<EPI_F32, false>(s->stream, g1, WID, Wt[0], K0, B, K0, WID, f, 1, nk, ys, wms[0]);
         }
     }
+    if (mid) cudaEventRecord(mid, s->stream);  // data gradients done
     // weight gradients over all steps at once: dW = op(A_all)^T dY_all (split-K)
     const long rows = (long)T * B;
     const int split = (int)std::min<long>(16, std::max<long>(1, rows / 4096));
@@ -1826,6 +1828,35 @@ int sur_train_step(sur_ctx *s, const float *U, const float *Y, int B, int T, flo
         for (int k = 0; k < s->K; k++) loss[k] = l[k] / ((double)B * T * NOUT);
     }
     return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+}
+
+int sur_profile_step(sur_ctx *s, const float *U, const float *Y, int B, int T, double *ms_out) {
+    if (!s || !U || !Y || !ms_out) return RC_EINVAL;
+    if (check_batch(s, B, T) != RC_OK) return RC_EINVAL;
+    const long s_ms = (long)B * T * NOUT;
+    cudaEvent_t ev[4];
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return RC_ECUDA;
+    cudaMemsetAsync(s->loss_acc, 0, sizeof(double) * s->K, s->stream);
+    cudaEventRecord(ev[0], s->stream);
+    if (s->backend == 2) {
+        forward_fused(s, 0, s->K, U, B, T, s->S, s_ms, T * NOUT, nullptr, nullptr, 0, true);
+        cudaEventRecord(ev[1], s->stream);
+        backward_members(s, 0, s->K, Y, B, T, s->S, s_ms, ev[2]);
+    } else {  // per member: the phases summed over the members
+        for (int k = 0; k < s->K; k++) forward(s, k, U, B, T, s->S + k * s_ms, nullptr);
+        cudaEventRecord(ev[1], s->stream);
+        for (int k = 0; k < s->K; k++) backward_members(s, k, 1, Y, B, T, s->S + k * s_ms, 0);
+        cudaEventRecord(ev[2], s->stream);
+    }
+    cudaEventRecord(ev[3], s->stream);
+    int rc = cudaEventSynchronize(ev[3]) == cudaSuccess ? RC_OK : RC_ECUDA;
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int i = 0; i < 3 && rc == RC_OK; i++)
+        if (cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]) != cudaSuccess) rc = RC_ECUDA;
+    for (int i = 0; i < 3; i++) ms_out[i] = t[i];
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc == RC_OK && cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
 }
 
 int sur_predict(sur_ctx *s, const float *U, int B, int T, float *Sout) {

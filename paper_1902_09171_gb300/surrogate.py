@@ -14,7 +14,8 @@ from . import rcell
 SUR_N_IN, SUR_N_H, SUR_N_OUT, SUR_WIDTH = 15, 128, 6, 256
 SUR_N_PARAMS = 144 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 144 + 144
 EXPORTS = ["sur_create", "sur_set_scaling", "sur_get_params", "sur_set_params", "sur_loss_grad", "sur_train_step",
-           "sur_predict", "sur_step", "sur_features", "sur_set_backend", "sur_sync", "sur_info", "sur_destroy"]
+           "sur_predict", "sur_profile_step", "sur_step", "sur_features", "sur_set_backend", "sur_sync", "sur_info",
+           "sur_destroy"]
 _bound = False
 
 
@@ -31,6 +32,7 @@ def _lib():
             "sur_loss_grad": ([vp, C.c_int, vp, vp, C.c_int, C.c_int, C.POINTER(C.c_double), vp], C.c_int),
             "sur_train_step": ([vp, vp, vp, C.c_int, C.c_int, C.c_float, C.c_float, vp], C.c_int),
             "sur_predict": ([vp, vp, C.c_int, C.c_int, vp], C.c_int),
+            "sur_profile_step": ([vp, vp, vp, C.c_int, C.c_int, vp], C.c_int),
             "sur_step": ([vp, vp, C.c_int, vp, C.c_float, vp, vp], C.c_int),
             "sur_features": ([vp, vp, C.c_int, vp, vp], C.c_int),
             "sur_info": ([vp, C.POINTER(C.c_int), C.POINTER(vp)], C.c_int),
@@ -103,6 +105,15 @@ def sur_train_step(s, U, Y, lr, wd=0.01, n_members=1, want_loss=True):
 def sur_predict(s, U, out):
     B, T = int(U.shape[0]), int(U.shape[1])
     _chk(_lib().sur_predict(s, _dp(U), B, T, _dp(out)), "sur_predict")
+
+
+def sur_profile_step(s, U, Y):
+    """Milliseconds of the phases of one training step (not applied): forward
+    with the tape, data gradients, weight and bias gradients."""
+    B, T = int(U.shape[0]), int(U.shape[1])
+    ms = np.zeros(3)
+    _chk(_lib().sur_profile_step(s, _dp(U), _dp(Y), B, T, C.c_void_p(ms.ctypes.data)), "sur_profile_step")
+    return {"forward_tape": float(ms[0]), "backward": float(ms[1]), "weight_grad": float(ms[2])}
 
 
 def sur_step(s, u, h, s_floor, s_mean, spread):

@@ -160,3 +160,22 @@ def test_member_batched_training_step_matches_oracle(torch):
         agree = np.mean(np.sign(step[big]) == -np.sign(gr[big]))
         assert agree > 0.99, (k, agree)
         assert np.abs(step[big]).max() <= 1.01 * lr
+
+
+def test_profile_step_times_the_phases_and_changes_no_parameter(torch):
+    B, T, K = 150, 8, 2
+    thetas = [problem(90 + k, B, T)[0] for k in range(K)]
+    _, U, Y = problem(91, B, T)
+    s = S.sur_create(K, B, T, 0)
+    try:
+        for k in range(K):
+            S.sur_set_params(s, k, thetas[k])
+        dU = torch.tensor(U, dtype=torch.float32, device="cuda")
+        dY = torch.tensor(Y, dtype=torch.float32, device="cuda")
+        ph = S.sur_profile_step(s, dU, dY)
+        assert S.sur_sync(s) == 0
+        assert set(ph) == {"forward_tape", "backward", "weight_grad"} and min(ph.values()) > 0.0
+        for k in range(K):
+            assert np.array_equal(S.sur_get_params(s, k), thetas[k])
+    finally:
+        S.sur_destroy(s)
