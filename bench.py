@@ -440,6 +440,7 @@ def run_kg_bar(args):
     if st != 0:
         raise RuntimeError("KG warm-up increments: " + rcell.rcell_last_error(ctx))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rb0 = rcell.rcell_get_rebuilds(ctx)
     for k in range(args.steps):
         ev[k][0].record(stream)
         rcell.fe_step(fe, ctx, 0.3 * (args.warmup + k + 1) / 60, md, md // 2, None)
@@ -447,6 +448,8 @@ def run_kg_bar(args):
     torch.cuda.synchronize()
     st = rcell.rcell_sync(ctx)
     ms = sum(a.elapsed_time(b) for a, b in ev)
+    rebuilds = (rcell.rcell_get_rebuilds(ctx) - rb0) / float(args.steps)  # per cell and increment
+    prof = rcell.rcell_profile_kernels(ctx, args.profile_steps)
     n_atoms = int(sizes.sum())
     Fe = np.zeros((len(cells), 3, 3))
     rcell.fe_get_F(fe, Fe)
@@ -456,7 +459,9 @@ def run_kg_bar(args):
            "status": rcell.STATUS[st], "data": "synthetic",
            "config": {"workload": f"kg_bar_{len(cells)}_cells_5k_20k", "atoms": n_atoms, "md_steps": md},
            "fe_load_steps_per_s": args.steps / (ms / 1e3),
-           "element_F_xx_range": [float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max())]}
+           "element_F_xx_range": [float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max())],
+           "list_rebuilds_per_cell_per_increment": round(float(np.mean(rebuilds)), 2),
+           "kernel_ms": {k: round(v, 5) for k, v in prof.items()}}
     rcell.fe_destroy(fe)
     rcell.rcell_destroy(ctx)
     return out

@@ -117,24 +117,36 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     if (threadIdx.x == 0) bs[nbt] = n;
     __syncthreads();
 
-    // stable ranking inside bins: one warp walks the atoms in their current order
+    // stable ranking inside bins: one warp walks the atoms in their current
+    // order, 32 at a time; the bin ids of the next RANK_BATCH chunks are loaded
+    // before the (smem-only) serial pass over them, so that the loads overlap
     if (threadIdx.x < 32) {
+        constexpr int RANK_BATCH = 16;
         const int lane = threadIdx.x;
         const unsigned lt = (1u << lane) - 1u;
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
-            const bool valid = i < n;
-            const int bin = valid ? a.binid[off + i] : -1 - lane;
-            const unsigned m = __match_any_sync(0xffffffffu, bin);
-            const int leader = __ffs(m) - 1;
-            int start = 0;
-            if (valid && lane == leader) {
-                start = s_cnt[bin];
-                s_cnt[bin] = start + __popc(m);
+        for (int base0 = 0; base0 < n; base0 += 32 * RANK_BATCH) {
+            int bins[RANK_BATCH];
+#pragma unroll
+            for (int k = 0; k < RANK_BATCH; k++) {
+                const int i = base0 + 32 * k + lane;
+                bins[k] = i < n ? a.binid[off + i] : -1 - lane;
             }
-            start = __shfl_sync(0xffffffffu, start, leader);
-            if (valid) a.newpos[off + i] = start + __popc(m & lt);
-            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < RANK_BATCH; k++) {
+                const int i = base0 + 32 * k + lane;
+                const bool valid = i < n;
+                const int bin = bins[k];
+                const unsigned m = __match_any_sync(0xffffffffu, bin);
+                const int leader = __ffs(m) - 1;
+                int start = 0;
+                if (valid && lane == leader) {
+                    start = s_cnt[bin];
+                    s_cnt[bin] = start + __popc(m);
+                }
+                start = __shfl_sync(0xffffffffu, start, leader);
+                if (valid) a.newpos[off + i] = start + __popc(m & lt);
+                __syncwarp();
+            }
         }
     }
     __syncthreads();
