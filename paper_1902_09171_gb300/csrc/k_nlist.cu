@@ -220,17 +220,30 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                     if ((slot == RC_SLOT_CENTRAL) != (sweep == 0)) continue;
                     const int bb = (u0 * nb1 + u1) * nb2 + u2;
                     const int j0 = bs[bb], j1 = bs[bb + 1];
-                    for (int jl = j0; jl < j1; jl++) {
-                        if (jl == li && slot == RC_SLOT_CENTRAL) continue;
-                        if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
-                        const float4 xj = X[off + jl];
-                        const float3 d = rc_disp(xi, xj, s_tab, slot);
-                        const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-                        if (r2 < p.rlist2) {
-                            if (cnt < p.max_nb)
-                                nbr[(size_t)(cnt >> 2) * (4 * RC_TILE) + (cnt & 3)] =
-                                    (int)((unsigned)(off + jl) | ((unsigned)slot << RC_IDX_BITS));
-                            cnt++;
+                    // one shift-table read per bin (the bin has one image slot); the
+                    // candidates' records are loaded NBATCH at a time so that their
+                    // loads overlap, then tested in order
+                    const float4 sa = s_tab.a[slot], sb = s_tab.b[slot];
+                    const float4 xs = make_float4(xi.x - sb.x, xi.y - sb.y, xi.z - sb.z, sb.w);
+                    constexpr int NBATCH = 8;
+                    for (int jb = j0; jb < j1; jb += NBATCH) {
+                        float4 xj[NBATCH];
+#pragma unroll
+                        for (int k = 0; k < NBATCH; k++) xj[k] = X[off + (jb + k < j1 ? jb + k : j1 - 1)];
+#pragma unroll
+                        for (int k = 0; k < NBATCH; k++) {
+                            const int jl = jb + k;
+                            if (jl >= j1) break;
+                            if (jl == li && slot == RC_SLOT_CENTRAL) continue;
+                            if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
+                            const float3 d = rc_disp_pre(xj[k], sa, xs);
+                            const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                            if (r2 < p.rlist2) {
+                                if (cnt < p.max_nb)
+                                    nbr[(size_t)(cnt >> 2) * (4 * RC_TILE) + (cnt & 3)] =
+                                        (int)((unsigned)(off + jl) | ((unsigned)slot << RC_IDX_BITS));
+                                cnt++;
+                            }
                         }
                     }
                 }
