@@ -331,7 +331,7 @@ def run_oracle_sample(n_cells_sample, md_steps, threads):
         Q, R = oracle.qr(F)
         x = oracle.remap(cells[c]["x0"], oracle.delta_R(R, np.eye(3)))
         _, _, _, ss, _, _ = oracle.md_run(pot, mdp, x, cells[c]["v0"], R @ cells[c]["H0"], cell=c, ev=0,
-                                          n_steps=md_steps, n_avg=md_steps // 2)
+                                          n_steps=md_steps, n_avg=max(1, md_steps // 2))
         s_fem = np.array([oracle.rotate_pk1(Q, F, s)[0] for s in ss])
         return s_fem.mean(0)
 
