@@ -40,8 +40,11 @@ typedef struct sur_ctx sur_ctx;
 
 /* Create n_members networks (seeded init: uniform +-1/sqrt(fan_in) weights,
  * zero biases, member m seeded with seed + m), with work buffers for up to
- * max_batch sequences of up to max_steps increments.  u_scale = 1, s_scale = 1.
- * Synchronous.  Errors: RC_EINVAL, RC_ENOMEM, RC_ECUDA. */
+ * max_batch sequences of up to max_steps increments.  The BPTT buffers are
+ * held once per member (about 5.2 KB per sequence-increment and member:
+ * inputs, pre-activations, activations and their gradients in BF16), so that
+ * the members train side by side.  u_scale = 1, s_scale = 1.  Synchronous.
+ * Errors: RC_EINVAL, RC_ENOMEM, RC_ECUDA. */
 int sur_create(int n_members, int max_batch, int max_steps, uint64_t seed, void *stream, sur_ctx **out);
 
 /* Feature and stress scales (host, 15 and 6 floats, all > 0). */
