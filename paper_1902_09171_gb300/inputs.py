@@ -220,8 +220,10 @@ def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, m
                  jitter: float = 0.01, max_lateral: float = 0.1):
     """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I).
 
-    Axial stretch along x: monotone or cyclic, amplitude up to max_strain in
-    tension and half of it in compression.  Each lateral stretch (y, z) is
+    Axial stretch along x: a monotone ramp to an amplitude drawn from
+    [-max_strain / 2, max_strain], or one to three sine cycles of that amplitude
+    growing as sqrt(t), which swing to minus the amplitude as well (so cyclic
+    paths reach max_strain in compression too).  Each lateral stretch (y, z) is
     -nu * eps_x (nu in [0, 0.5]) plus its own drift that saturates on a random
     time scale (from a few increments to the whole path), between -max_lateral
     and +max_lateral / 4 -- so paths include lateral contraction at zero axial
