@@ -1,8 +1,11 @@
 // Recurrent-MLP stress surrogate on tensor cores: BF16 operands, FP32
-// accumulation, fused epilogues, BPTT and AdamW.  Two GEMM engines: tcgen05
-// (5th-generation tensor cores, accumulator in tensor memory; the default for
-// the forward and data-gradient products) and warp-level mma.sync m16n8k16
-// (weight gradients, which read A transposed, and the alternative engine).
+// accumulation, fused epilogues, BPTT and AdamW.  The default engine runs on
+// tcgen05 (5th-generation tensor cores, accumulators in tensor memory): the
+// whole forward and the whole BPTT data-gradient chain each in one
+// warp-specialised kernel (k_forward_ws, k_backward_ws), the weight and bias
+// gradients in k_wgrad_tc05, all members side by side.  The alternative
+// engines run one GEMM per layer and step, on tcgen05 (k_gemm_tc05) or on
+// warp-level mma.sync m16n8k16 (k_gemm).
 //
 // mma.sync GEMM: C[M x N] = op(A)[M x K] * B[K x N], op(A) = A (row-major, lda) or A^T
 // (A stored K x M).  CTA tile 64 x 64 x 32, four warps of 32 x 32; operand
