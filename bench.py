@@ -468,7 +468,7 @@ def run_kg_bar(args):
 
 
 def run_kg_statics(args):
-    """The paper's molecular-statics r-cell route (Sec. 2.1, Eqs. CGPR1-CGPR3, PK1)
+    """The paper's molecular-statics r-cell route (Sec. 2.2, Eqs. CGPR1-CGPR3, PK1)
     on amorphous Kremer-Grest cells: 32 cells of 5000 beads, quenched to a local
     energy minimum; one bench step = one load increment of uniaxial stretch (0.5 %)
     through rcell_set_deformation (the Cauchy-Born guess), FIRE relaxation of every

@@ -71,7 +71,7 @@ enum { RC_UNITS_METAL = 0, RC_UNITS_LJ = 1 };
  *   RC_POT_SC : Sutton-Chen EAM, E = eps [1/2 sum_i sum_j!=i (a/r)^n
  *               - c sum_i sqrt(rho_i)], rho_i = sum_j!=i (a/r)^m, r < rc;
  *               `sigma` holds a.
- *   RC_POT_KG : Kremer-Grest bead-spring (Sec. 2.2): LJ (eps, sigma, rc) between
+ *   RC_POT_KG : Kremer-Grest bead-spring (Sec. 3.2): LJ (eps, sigma, rc) between
  *               non-bonded pairs; bonded pairs get FENE
  *               -1/2 k_fene R0^2 ln(1 - (r/R0)^2) plus WCA (LJ cut and shifted
  *               at 2^{1/6} sigma) and no non-bonded LJ.
@@ -113,16 +113,18 @@ typedef struct {
 /* Create a batch of n_cells r-cells (uneven atom counts allowed) on the current
  * CUDA device.  stream: a cudaStream_t (NULL = default stream).  Copies all
  * inputs; *out receives the context.  Errors: RC_EINVAL (bad sizes/params,
- * box thinner than 2 r_list), RC_ENOMEM, RC_ECUDA.  Synchronous. */
+ * non-finite H0, x0 or v0, box thinner than 2 r_list), RC_ENOMEM, RC_ECUDA.
+ * Synchronous. */
 int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cells, void *stream, rcell_ctx **out);
 
 /* Sec. 2.1 + Eq. LAMMPS2: for every cell c take F_c (n_cells x 9 doubles,
  * row-major), factor F = Q R with R_ii > 0 (FP64 Gram-Schmidt on the GPU),
  * set the box to R H0, remap atom positions x <- (R R_prev^{-1}) x (FP64 math on
  * the FP32 positions; velocities unchanged) and schedule a neighbour rebuild.
- * where: location of F.  Cells with det F <= 0 get RC_EDEGEN and keep their
- * previous state; cells whose new box is thinner than 2 r_list get RC_EBOX.
- * Asynchronous. */
+ * where: location of F.  A host F with a non-finite entry is refused with
+ * RC_EINVAL before any launch.  Cells with det F <= 0 get RC_EDEGEN and keep
+ * their previous state; cells whose new box is thinner than 2 r_list get
+ * RC_EBOX.  Asynchronous. */
 int rcell_set_deformation(rcell_ctx *ctx, const double *F, int where);
 
 /* Run n_steps fixed-box MD steps on every cell (one setup force evaluation +
@@ -180,13 +182,33 @@ int rcell_get_series(rcell_ctx *ctx, int cell, double *stress, double *pe, doubl
 /* Wait for the stream; return the first per-cell error (or RC_OK). */
 int rcell_sync(rcell_ctx *ctx);
 
-/* Clear the per-cell error words (after the caller has handled them). */
+/* Clear the per-cell error words (after the caller has handled them).  A cell
+ * whose error arose inside a run stopped there: it holds the positions of the
+ * step that failed or of the one before, so restore a checkpoint of it
+ * (rcell_restore) before running it again where that matters. */
 int rcell_clear_status(rcell_ctx *ctx);
 
 /* Tuning knobs (chosen by the autotuner; any value < 0 keeps the current):
  *   threads_per_atom : 1, 2, 4 or 8 lanes cooperate on one atom's neighbours
  *   use_graphs       : 0/1, capture rcell_run into CUDA graphs */
 int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
+
+/* Failure-injection limits, with no counterpart in the paper (any value < 0
+ * keeps the current one):
+ *   max_neighbors : per-atom Verlet-list capacity used from now on, a multiple
+ *                   of 4 in [4, the capacity allocated at creation]; 0 restores
+ *                   that capacity.  Lists that would hold more entries are
+ *                   truncated and the cell reports RC_EOVERFLOW.  Every list is
+ *                   rebuilt at the next step.
+ *   wait_polls    : polls of the bounded device-side wait of the shared-memory
+ *                   staging (rcell_set_staging) before it gives up with
+ *                   RC_ETIMEOUT; RC_WAIT_POLLS_DEFAULT at creation.  A wait
+ *                   that gives up still lets the copies it issued land before
+ *                   its block exits.
+ * RC_EINVAL for a capacity outside the range.  Synchronises the stream when a
+ * value changes. */
+#define RC_WAIT_POLLS_DEFAULT (1 << 22)
+int rcell_set_limits(rcell_ctx *ctx, int max_neighbors, int wait_polls);
 
 /* Shared-memory staging of whole r-cells: with 1, every CTA first copies its
  * r-cell's records into shared memory (TMA bulk copy) and gathers neighbours
@@ -195,7 +217,7 @@ int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
  * read-only cache.  Both give the same results up to summation order. */
 int rcell_set_staging(rcell_ctx *ctx, int staged);
 
-/* Molecular statics (Sec. 2.1, Eq. CGPR1): relax the atoms of every active
+/* Molecular statics (Sec. 2.2, Eq. CGPR1): relax the atoms of every active
  * cell without an error at fixed box to a local minimum of the potential
  * energy, starting from the current positions (after rcell_set_deformation
  * these are the Cauchy-Born guess F H(0) S of the previous configuration, the
@@ -212,7 +234,7 @@ int rcell_set_staging(rcell_ctx *ctx, int staged);
 int rcell_minimize(rcell_ctx *ctx, int max_iter, double f_tol, double dt0, double dt_max, double dmax,
                    int *iters_out);
 
-/* Eq. PK1 / Eq. CGPR2 (Sec. 2.1): the first Piola-Kirchhoff stress of every
+/* Eq. PK1 / Eq. CGPR2 (Sec. 2.2): the first Piola-Kirchhoff stress of every
  * cell from the pair sum over its current positions,
  *   P_MD = 1/(2 Omega_0) sum_{i != j} dE/dr_ij r_ij (x) R_ij / r_ij,
  * with R_ij = H(0) H^{-1} r_ij the separation in the reference box and
@@ -261,12 +283,13 @@ int rcell_profile_kernels(rcell_ctx *ctx, int n_steps, double *ms_out);
 int rcell_checkpoint(rcell_ctx *ctx, int cell, void *buf, size_t *bytes);
 int rcell_restore(rcell_ctx *ctx, int cell, const void *buf, size_t bytes);
 
-/* Allocation-free stress reduction, for callers that cannot allocate device
- * memory when they need the stress (inside a stream capture under the global
- * capture mode, from a stream callback, or under a fixed up-front memory
- * budget).  The paper has no counterpart: it is the reduction of rcell_stress
- * taken out of the context, with its scratch in a fixed device array of the
- * library instead of memory the context allocated.
+/* Allocation-free stress reduction, for callers that cannot call cudaMalloc
+ * when they need the stress: a host program that reserves the GPU's memory up
+ * front for its own pool and forbids later device allocations, or a
+ * latency-bound loop that must not take the implicit device synchronisation of
+ * cudaFree / a growing cudaMalloc.  The paper has no counterpart: it is the
+ * reduction of rcell_stress taken out of the context, with its scratch in a
+ * fixed device array of the library instead of memory the context allocated.
  *   series       device, n_cells x n_avg x 6: MD-frame tension-positive stress
  *                samples (Voigt), e.g. what rcell_get_series returns
  *   Q, F         device, n_cells x 9 each: rotation and deformation gradient
@@ -275,9 +298,12 @@ int rcell_restore(rcell_ctx *ctx, int cell, const void *buf, size_t bytes);
  *   P            device, n_cells x 9 or NULL: J sigma F^{-T}
  *   stream       cudaStream_t to enqueue on (NULL = default stream)
  * n_cells * n_avg must not exceed 65536 (RC_EINVAL otherwise, nothing runs).
- * Allocates nothing.  All calls share the scratch array: calls whose kernels
+ * Allocates nothing and calls no allocating routine.  All calls share the
+ * scratch array, which keeps the last call's contents: calls whose kernels
  * overlap on the GPU race.  The first call on a device looks the array up
- * (device current); make it before any stream capture.  Asynchronous. */
+ * (device current); make it before any stream capture.  RC_ECUDA when the
+ * launch itself fails (an unrelated earlier error is not reported).
+ * Asynchronous. */
 int rcell_stress_reduce_static(const double *series, int n_cells, int n_avg, const double *Q, const double *F,
                                double *sigma, double *sigma_stderr, double *P, void *stream);
 
@@ -303,7 +329,7 @@ int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mas
               double rho0, double dt, double damping, double hg_coef, void *stream, fe_ctx **out);
 
 /* The same explicit FE with 4-node tetrahedra, the element the paper uses
- * (C3D4, Sec. 2.2): shape functions N = (1 - xi - eta - zeta, xi, eta, zeta)
+ * (C3D4, Sec. 3.2): shape functions N = (1 - xi - eta - zeta, xi, eta, zeta)
  * on the reference tetrahedron, so grad N and F = I + sum_a d_a (x) grad N_a
  * are constant in the element (one quadrature point, one r-cell per element)
  * and there are no hourglass modes (no stabilisation).  Lumped mass

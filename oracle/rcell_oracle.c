@@ -816,7 +816,7 @@ void or_fe_update(int nn, const double *X, int ne, const int *conn, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* 4-node tetrahedra, the paper's element (C3D4, Sec. 2.2): linear shape     */
+/* 4-node tetrahedra, the paper's element (C3D4, Sec. 3.2): linear shape     */
 /* functions N = (1 - xi - eta - zeta, xi, eta, zeta), so grad N and F are    */
 /* constant in the element; one quadrature point (one r-cell), no hourglass  */
 /* modes.  Lumped mass rho0 V / 4 per node; the same explicit update.        */
@@ -893,7 +893,7 @@ void or_fe_tet_update(int nn, int ne, const int *conn, const double *gradN, cons
 }
 
 /* ------------------------------------------------------------------------ */
-/* Molecular statics of an r-cell (Sec. 2.1, Eqs. CGPR1-CGPR3 and PK1).      */
+/* Molecular statics of an r-cell (Sec. 2.2, Eqs. CGPR1-CGPR3 and PK1).      */
 /* ------------------------------------------------------------------------ */
 
 /*

@@ -1,4 +1,4 @@
-// Molecular statics of the r-cells (Sec. 2.1, Eqs. CGPR1-CGPR3, PK1): energy
+// Molecular statics of the r-cells (Sec. 2.2, Eqs. CGPR1-CGPR3, PK1): energy
 // minimisation at fixed box by FIRE (Bitzek, Koskinen, Gaehler, Moseler and
 // Gumbsch, Phys. Rev. Lett. 97, 170201, 2006), cell by cell in one batch, and
 // the reduction of the pair-sum first Piola-Kirchhoff stress.

@@ -47,8 +47,11 @@ constexpr int RC_SPIN_LIMIT = 1 << 22;
 
 // Copy n float4 records (16-byte aligned) from global memory into shared memory
 // with TMA bulk copies that complete on one mbarrier; every thread waits with a
-// bounded spin.  On a timeout the cell is flagged RC_ETIMEOUT and false returned.
-__device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, int n, int *status, int c) {
+// bounded spin of `polls` polls.  On a timeout the cell is flagged RC_ETIMEOUT
+// and false returned, after a second wait (RC_SPIN_LIMIT polls, independent of
+// `polls`) for the copies already issued, so that none is in flight when the
+// CTA leaves.
+__device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, int n, int *status, int c, int polls) {
     __shared__ __align__(8) unsigned long long s_bar;
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar);
     const unsigned bytes = (unsigned)n * 16u;
@@ -69,7 +72,7 @@ __device__ __forceinline__ bool stage_records(float4 *dst, const float4 *src, in
         }
     }
     unsigned done = 0;
-    for (int it = 0; it < RC_SPIN_LIMIT && !done; it++)
+    for (int it = 0; it < polls && !done; it++)
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
     const float4 *__restrict__ X = cur ? a.x1 : a.x0;
-    if (STG && !stage_records(s_cell, X + off, n, a.status, c)) return;
+    if (STG && !stage_records(s_cell, X + off, n, a.status, c, p.wait_polls)) return;
     const bool live = li < n;
     const int g = off + li;
     float rho = 0.0f;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     const int g = off + li;
     const float4 *__restrict__ X = cur ? a.x1 : a.x0;
     const float4 *__restrict__ XG = (POT == RC_POT_SC) ? a.xr : X;  // gathered array
-    if (STG && !stage_records(s_cell, XG + off, n, a.status, c)) return;
+    if (STG && !stage_records(s_cell, XG + off, n, a.status, c, p.wait_polls)) return;
 
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;  // xx yy zz xy xz yz
@@ -513,7 +516,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     }
 }
 
-// Eq. PK1 (Sec. 2.1): per cell, the sum over ordered pairs inside rc of
+// Eq. PK1 (Sec. 2.2): per cell, the sum over ordered pairs inside rc of
 // dE/dr_ij r_ij (x) R_ij / r_ij with R_ij = M r_ij, M = H(0) H^{-1} (upper
 // triangular, m[6] per cell: m00 m01 m02 m11 m12 m22), plus the Kremer-Grest
 // bonds, each seen from both ends.  FP32 per atom, FP64 per cell into

@@ -244,6 +244,19 @@ __global__ void __launch_bounds__(STRESS_THREADS) k_stress(const double *__restr
     }
 }
 
+// Cells skipped by a run (activity mask 0) keep their positions in the buffer
+// that was current when the run began; after an odd number of steps the other
+// buffer is current, so their positions are copied into it.
+__global__ void __launch_bounds__(RC_TILE) k_keep_frozen(KArrays a, int cur_new) {
+    const int t = blockIdx.x;
+    const int c = a.tile_cell[t];
+    if (a.active[c]) return;
+    const int li = (t - a.cell_tile0[c]) * RC_TILE + threadIdx.x;
+    if (li >= a.cell_n[c]) return;
+    const int g = a.cell_off[c] + li;
+    (cur_new ? a.x1 : a.x0)[g] = (cur_new ? a.x0 : a.x1)[g];
+}
+
 __global__ void k_advance(unsigned long long *evals, const int *active, int n_cells, int n) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n_cells && active[c]) evals[c] += (unsigned long long)n;
@@ -267,6 +280,10 @@ void rc_launch_stress(const double *series, int n_avg, int series_cap, const dou
                       double *sig_md, double *P, int n_cells, cudaStream_t s) {
     k_stress<<<n_cells, STRESS_THREADS, 0, s>>>(series, n_avg, series_cap, H, Q, F, pconv, rot_scratch, sig_fem,
                                                 sig_se, sig_md, P);
+}
+
+void rc_launch_keep_frozen(const KArrays &a, int cur_new, int n_tiles, cudaStream_t s) {
+    k_keep_frozen<<<n_tiles, RC_TILE, 0, s>>>(a, cur_new);
 }
 
 void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s) {

@@ -1,28 +1,30 @@
 // Stress reduction that allocates nothing.
 //
-// Some callers cannot allocate device memory at the moment they need the
-// time-averaged stress: code that runs while a CUDA stream is being captured
-// into a graph under the global capture mode, code running from a stream
-// callback, or a host application that hands the GPU a fixed memory budget up
-// front and forbids later cudaMalloc calls.  rcell_stress_reduce_static gives
-// them the stress reduction of rcell_stress (rotation to the FE frame, mean,
-// blocking standard error, first Piola-Kirchhoff stress) with its only scratch
-// -- the rotated sample series -- in a fixed-size array that lives in this
-// library's device image.  The caller passes inputs and outputs; the library
-// allocates nothing, in this call or anywhere else on its behalf.
+// Some callers cannot call cudaMalloc at the moment they need the
+// time-averaged stress: a host program that reserves the GPU's memory up front
+// for its own pool and forbids any later device allocation, or a latency-bound
+// loop that must not take the implicit device-wide synchronisation that
+// cudaFree (and, when it has to grow the heap, cudaMalloc) performs.
+// rcell_stress_reduce_static gives them the stress reduction of rcell_stress
+// (rotation to the FE frame, mean, blocking standard error, first
+// Piola-Kirchhoff stress) with its only scratch -- the rotated sample series --
+// in a fixed-size array that lives in this library's device image.  The caller
+// passes inputs and outputs; the call allocates nothing and calls no
+// allocating library routine.
 //
 // Limits and sharing:
 //   * The scratch holds RC_STATIC_SCRATCH_SAMPLES six-component samples
 //     (3 MiB of FP64); n_cells * n_avg above that is rejected with RC_EINVAL
 //     before any GPU work.  Every GPU that loads the library holds the array
 //     until the process exits.
-//   * All calls share the one array.  Each call writes every scratch entry it
-//     reads before reading it, so leftovers of an earlier call never matter,
-//     but two calls whose kernels overlap on the GPU (different streams, no
-//     ordering between them) race on the array and give wrong results.
+//   * All calls share the one array, which keeps the last call's contents.
+//     Each call writes every scratch entry it reads before reading it, so
+//     leftovers of an earlier call never matter, but two calls whose kernels
+//     overlap on the GPU (different streams, no ordering between them) race on
+//     the array and give wrong results.
 //   * The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress while that device is current; make that first call
-//     outside any stream capture.
+//     before any stream capture.
 #include <mutex>
 
 #include "rc_internal.cuh"
@@ -156,7 +158,12 @@ extern "C" int rcell_stress_reduce_static(const double *series, int n_cells, int
         }
         rot = g_rot_ptr[dev];
     }
-    k_stress_static<<<n_cells, ST_THREADS, 0, (cudaStream_t)stream>>>(series, n_avg, Q, F, rot, sigma,
-                                                                       sigma_stderr, P);
-    return cudaGetLastError() == cudaSuccess ? RC_OK : RC_ECUDA;
+    // the launch's own return code: an error left behind by an unrelated
+    // earlier call is neither reported nor cleared here
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_cells);
+    cfg.blockDim = dim3(ST_THREADS);
+    cfg.stream = (cudaStream_t)stream;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_stress_static, series, n_avg, Q, F, rot, sigma, sigma_stderr, P);
+    return e == cudaSuccess ? RC_OK : RC_ECUDA;
 }

@@ -49,6 +49,7 @@ struct KParams {
     float max_step;       // > 0: displacement limit per step
     int n_tiles;          // tiles of RC_TILE atoms in the batch
     int n_sm;             // SMs of the device (tile order of the pair kernels)
+    int wait_polls;       // polls of a bounded device-side wait before it gives up
 };
 
 struct KArrays {
@@ -242,6 +243,7 @@ void rc_launch_static_prep(const double *H, const double *H0, float *mcell, doub
 void rc_launch_static_finish(const double *acc, const double *H0, const double *Q, const double *F, double pconv,
                              double *P, double *sig, const int *status, int n_cells, cudaStream_t st);
 void rc_launch_advance(unsigned long long *evals, const int *active, int n_cells, int n, cudaStream_t s);
+void rc_launch_keep_frozen(const KArrays &a, int cur_new, int n_tiles, cudaStream_t s);
 
 // finite elements (k_fe.cu)
 void fe_launch_geometry(int npe, const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,

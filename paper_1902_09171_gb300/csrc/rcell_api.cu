@@ -49,6 +49,7 @@ struct rcell_ctx {
     int tpa = 1;
     int use_graphs = 1;
     int max_cell = 0;    // largest cell of the batch (atoms)
+    int max_nb_alloc = 0;  // neighbour-list entries per atom allocated at creation
     int staged = 0;      // stage whole cells in shared memory (when they fit) -- off by default
     long launches_last = 0;
     // molecular statics (allocated on first use)
@@ -155,6 +156,10 @@ long enqueue_run(rcell_ctx *c, int n_steps, int n_avg) {
         k += enqueue_step(c, mode, slot, s);
         if (mode != MODE_LAST) c->cur ^= 1;
     }
+    if (n_steps & 1) {  // frozen cells: their positions into the buffer that is current now
+        rc_launch_keep_frozen(c->ka, c->cur, c->n_tiles, c->stream);
+        k++;
+    }
     rc_launch_advance(c->d_evals, c->ka.active, c->n_cells, n_steps + 1, c->stream);
     return k + 1;
 }
@@ -217,6 +222,14 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     for (int i = 0; i < n_cells; i++) {
         const rcell_init &ci = cells[i];
         if (ci.n_atoms <= 0 || !ci.H0 || !ci.x0) { rcell_destroy(c); return RC_EINVAL; }
+        // non-finite inputs are refused before anything reaches the device
+        bool finite = true;
+        for (int k = 0; k < 9; k++) finite = finite && std::isfinite(ci.H0[k]);
+        for (long k = 0; k < 3L * ci.n_atoms; k++) {
+            finite = finite && std::isfinite(ci.x0[k]);
+            if (ci.v0) finite = finite && std::isfinite(ci.v0[k]);
+        }
+        if (!finite) { rcell_destroy(c); return RC_EINVAL; }
         if (ci.H0[3] != 0.0 || ci.H0[6] != 0.0 || ci.H0[7] != 0.0) { rcell_destroy(c); return RC_EINVAL; }
         const double V = ci.H0[0] * ci.H0[4] * ci.H0[8];
         if (!(V > 0)) { rcell_destroy(c); return RC_EINVAL; }
@@ -272,6 +285,8 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
     kp.mvv2e = (float)(P.mass / ftm2v);
     kp.seed = P.seed;
     kp.max_nb = max_nb;
+    c->max_nb_alloc = max_nb;
+    kp.wait_polls = RC_WAIT_POLLS_DEFAULT;
     kp.n_tiles = c->n_tiles;
     kp.n_sm = 1;
     CKC(c, cudaDeviceGetAttribute(&kp.n_sm, cudaDevAttrMultiProcessorCount, c->device));
@@ -409,6 +424,8 @@ int rcell_set_deformation(rcell_ctx *c, const double *F, int where) {
     if (!c || !F) return RC_EINVAL;
     const double *dF = F;
     if (where == RC_HOST) {
+        for (long k = 0; k < 9L * c->n_cells; k++)
+            if (!std::isfinite(F[k])) return fail(c, RC_EINVAL, "non-finite deformation gradient");
         CKC(c, cudaMemcpyAsync(c->d_Fin, F, sizeof(double) * 9 * c->n_cells, cudaMemcpyHostToDevice, c->stream));
         dF = c->d_Fin;
     } else if (where != RC_DEVICE) {
@@ -602,6 +619,28 @@ int rcell_set_staging(rcell_ctx *c, int staged) {
     if (!c) return RC_EINVAL;
     if (staged >= 0 && (staged ? 1 : 0) != c->staged) {
         c->staged = staged ? 1 : 0;
+        free_graphs(c);
+    }
+    return RC_OK;
+}
+
+int rcell_set_limits(rcell_ctx *c, int max_neighbors, int wait_polls) {
+    if (!c) return RC_EINVAL;
+    if (max_neighbors >= 0) {
+        const int mx = max_neighbors == 0 ? c->max_nb_alloc : max_neighbors;
+        if (mx < 4 || mx % 4 != 0 || mx > c->max_nb_alloc)
+            return fail(c, RC_EINVAL, "max_neighbors must be 0 or a multiple of 4 in [4, the allocated capacity]");
+        if (mx != c->kp.max_nb) {
+            CKC(c, cudaStreamSynchronize(c->stream));
+            c->kp.max_nb = mx;
+            free_graphs(c);  // graphs hold the old parameters
+            std::vector<int> ones(c->n_cells, 1);  // every list is rebuilt with the new capacity
+            CKC(c, cudaMemcpy(c->ka.need_rebuild, ones.data(), sizeof(int) * c->n_cells, cudaMemcpyHostToDevice));
+        }
+    }
+    if (wait_polls >= 0 && wait_polls != c->kp.wait_polls) {
+        CKC(c, cudaStreamSynchronize(c->stream));
+        c->kp.wait_polls = wait_polls;
         free_graphs(c);
     }
     return RC_OK;
@@ -849,6 +888,7 @@ int rcell_profile_kernels(rcell_ctx *c, int n_steps, double *ms_out) {
         if (s > 0) lap(3, 4, slot >= 0 ? 7 : 3);  // steady-state force launches only
         if (mode != MODE_LAST) c->cur ^= 1;
     }
+    if (n_steps & 1) rc_launch_keep_frozen(c->ka, c->cur, c->n_tiles, c->stream);
     rc_launch_advance(c->d_evals, c->ka.active, c->n_cells, n_steps + 1, c->stream);
     c->last_n_avg = n_avg;
     if (c->last_n_avg > 0) {

@@ -1,9 +1,9 @@
 """Multi-GPU layout of the r-cell batch (one process per GPU).
 
-The r-cells of a load step are independent at the MD level (Sec. 2.2: the
+The r-cells of a load step are independent at the MD level (Sec. 2.3: the
 paper gives each r-cell its own communicator split), so the cells are split
 into contiguous, atom-balanced shards, one per rank, with no collective on the
-MD data path.  The only exchange is the FE-level one of Sec. 2.2 (scatter F,
+MD data path.  The only exchange is the FE-level one of Sec. 2.3 (scatter F,
 gather the stress): each rank contributes the stresses of its own cells and
 `gather_cells` assembles the full per-cell array on every rank.
 """

@@ -6,9 +6,9 @@ integrator, no QR, no stress).  Both the CUDA path and the FP64 oracle are fed
 from here, so neither depends on the other.
 
 Workload recipes (the paper's own data are not available; these stand in):
-  * Cu-like FCC crystals (Sec. 2.1 uses a 10x10x10 FCC Cu cell, 4000 atoms,
+  * Cu-like FCC crystals (Sec. 3.1 uses a 10x10x10 FCC Cu cell, 4000 atoms,
     edge 36.15 A): ``fcc(nx, ny, nz, a)`` with a = 3.615 A.
-  * Kremer-Grest melts (Sec. 2.2: linear bead-spring chains at melt density):
+  * Kremer-Grest melts (Sec. 3.2: linear bead-spring chains at melt density):
     ``kg_melt(n_chains, chain_len, density, seed)`` -- seeded random walks with
     bond length 0.97 sigma, then a displacement-capped soft push-off.
   * Maxwell velocities with zero centre-of-mass momentum.

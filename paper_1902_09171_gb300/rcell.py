@@ -47,7 +47,7 @@ class rcell_init(C.Structure):
 _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
-           "rcell_clear_status", "rcell_set_active", "rcell_set_staging", "rcell_set_tuning", "rcell_minimize", "rcell_stress_static", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
+           "rcell_clear_status", "rcell_set_active", "rcell_set_limits", "rcell_set_staging", "rcell_set_tuning", "rcell_minimize", "rcell_stress_static", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
            "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_create_tet4", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
@@ -77,6 +77,7 @@ def load(path: str | None = None):
         "rcell_clear_status": ([vp], C.c_int),
         "rcell_set_active": ([vp, vp, C.c_int], C.c_int),
         "rcell_set_staging": ([vp, C.c_int], C.c_int),
+        "rcell_set_limits": ([vp, C.c_int, C.c_int], C.c_int),
         "rcell_set_tuning": ([vp, C.c_int, C.c_int], C.c_int),
         "rcell_info": ([vp, I, C.POINTER(C.c_long), C.POINTER(C.c_long)], C.c_int),
         "rcell_profile_kernels": ([vp, C.c_int, vp], C.c_int),
@@ -258,6 +259,15 @@ def rcell_set_active(ctx, mask):
     _check(load().rcell_set_active(ctx, p, where), ctx, "rcell_set_active")
 
 
+RC_WAIT_POLLS_DEFAULT = 1 << 22
+
+
+def rcell_set_limits(ctx, max_neighbors: int = -1, wait_polls: int = -1):
+    """Failure-injection limits: per-atom list capacity (0 = as allocated) and polls
+    of the staging wait (values < 0 keep the current)."""
+    _check(load().rcell_set_limits(ctx, int(max_neighbors), int(wait_polls)), ctx, "rcell_set_limits")
+
+
 def rcell_set_staging(ctx, staged: int):
     _check(load().rcell_set_staging(ctx, int(staged)), ctx, "rcell_set_staging")
 
@@ -336,9 +346,35 @@ def rcell_restore(ctx, cell: int, blob: bytes):
 
 
 def rcell_stress_reduce_static(series, Q, F, sigma, sigma_stderr=None, P=None, stream=None):
-    """Allocation-free stress reduction; all arrays are CUDA tensors (float64).
-    series: (n_cells, n_avg, 6); Q, F: (n_cells, 3, 3); outputs preallocated."""
+    """Allocation-free stress reduction; all arrays are CUDA float64 tensors of
+    the current device, contiguous: series (n_cells, n_avg, 6); Q, F
+    (n_cells, 3, 3); outputs preallocated: sigma (n_cells, 6), optional
+    sigma_stderr (n_cells, 6) and P (n_cells, 3, 3).  stream=None enqueues on
+    torch's current stream of the current device.  Anything else raises
+    RCellError(RC_EINVAL) before the library is called."""
+    import torch
+    if series is None or series.dim() != 3 or series.shape[2] != 6:
+        raise RCellError(CODES["RC_EINVAL"], "series must have shape (n_cells, n_avg, 6)")
     n_cells, n_avg = int(series.shape[0]), int(series.shape[1])
+    dev = torch.cuda.current_device()
+    shapes = {"series": (series, (n_cells, n_avg, 6)), "Q": (Q, (n_cells, 3, 3)), "F": (F, (n_cells, 3, 3)),
+              "sigma": (sigma, (n_cells, 6)), "sigma_stderr": (sigma_stderr, (n_cells, 6)),
+              "P": (P, (n_cells, 3, 3))}
+    for name, (t, shape) in shapes.items():
+        if t is None and name in ("sigma_stderr", "P"):
+            continue
+        if t is None or not hasattr(t, "data_ptr"):
+            raise RCellError(CODES["RC_EINVAL"], f"{name} must be a CUDA tensor")
+        if not t.is_cuda or t.device.index != dev:
+            raise RCellError(CODES["RC_EINVAL"], f"{name} must live on the current CUDA device ({dev})")
+        if t.dtype != torch.float64:
+            raise RCellError(CODES["RC_EINVAL"], f"{name} must be float64")
+        if not t.is_contiguous():
+            raise RCellError(CODES["RC_EINVAL"], f"{name} must be contiguous")
+        if tuple(t.shape) != shape:
+            raise RCellError(CODES["RC_EINVAL"], f"{name} has shape {tuple(t.shape)}, expected {shape}")
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
     ptr = [None if a is None else C.c_void_p(a.data_ptr()) for a in (series, Q, F, sigma, sigma_stderr, P)]
     _check(load().rcell_stress_reduce_static(ptr[0], n_cells, n_avg, ptr[1], ptr[2], ptr[3], ptr[4], ptr[5],
                                              _stream_ptr(stream)), None, "rcell_stress_reduce_static")

@@ -1,4 +1,4 @@
-"""The 4-node tetrahedron FE (the paper's C3D4 element, Sec. 2.2) on the GPU,
+"""The 4-node tetrahedron FE (the paper's C3D4 element, Sec. 3.2) on the GPU,
 through the C ABI: geometry, F, assembly and the explicit update against the
 FP64 oracle (FP64 on both sides: 1e-12), and an FE-MD coupled step with one
 r-cell per tetrahedron."""

@@ -1,4 +1,4 @@
-"""Molecular statics of the r-cells on the GPU (Sec. 2.1): FIRE relaxation at
+"""Molecular statics of the r-cells on the GPU (Sec. 2.2): FIRE relaxation at
 fixed box (Eq. CGPR1) and the pair-sum first Piola-Kirchhoff stress (Eq. PK1),
 against the FP64 oracle, through the C ABI.
 

@@ -1,5 +1,5 @@
 """Pins of the oracle's 4-node tetrahedron FE (the paper's C3D4 element,
-Sec. 2.2): closed-form shape-function gradients, linear completeness (patch
+Sec. 3.2): closed-form shape-function gradients, linear completeness (patch
 tests), traction balance, volume and mass, and convergence of the damped
 explicit update to the static bar."""
 import numpy as np

@@ -1,5 +1,5 @@
 """Pins of the oracle's force / energy / virial evaluation (the MD engine of Sec. 2.1
-and Sec. 2.2: LJ, Sutton-Chen EAM, Kremer-Grest FENE+WCA)."""
+and the polymer model of Sec. 3.2: LJ, Sutton-Chen EAM, Kremer-Grest FENE+WCA)."""
 import itertools
 
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the molecular-statics part of the FP64 oracle (Sec. 2.1):
+"""Pins of the molecular-statics part of the FP64 oracle (Sec. 2.2):
 Eq. PK1 (first Piola-Kirchhoff stress from the pair sum with reference
 separations) and the FIRE energy minimiser behind Eq. CGPR1."""
 import numpy as np

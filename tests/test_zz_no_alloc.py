@@ -1,11 +1,12 @@
 """The allocation-free stress reduction (rcell_stress_reduce_static) against the
 context's own reduction (rcell_stress).
 
-Callers that cannot allocate device memory at the time they reduce -- inside a
-global-mode stream capture, from a stream callback, under a fixed memory
-budget -- use the static entry point, whose only scratch is a fixed array in
-the library's device image.  This file runs last (pytest orders files by name)
-so that a failure here leaves every other test already run.
+Callers that cannot call cudaMalloc at the time they reduce -- a host program
+that reserves the GPU's memory up front for its own pool, a latency-bound loop
+that must not take the implicit device synchronisation of cudaFree -- use the
+static entry point, whose only scratch is a fixed array in the library's device
+image.  This file runs last (pytest orders files by name) so that a failure
+here leaves every other test already run.
 """
 import json
 import os
@@ -73,3 +74,24 @@ def test_static_reduction_rejects_oversized_input(torch):
     with pytest.raises(rcell.RCellError) as e:
         rcell.rcell_stress_reduce_static(series, Q, Q, out)
     assert e.value.name == "RC_EINVAL"
+
+
+def test_static_reduction_rejects_bad_tensors_before_the_call(torch):
+    # wrong dtype, layout or shape never reaches the kernel
+    dev = torch.device("cuda:0")
+    n_cells, n_avg = 2, 32
+    series = torch.zeros((n_cells, n_avg, 6), dtype=torch.float64, device=dev)
+    Q = torch.eye(3, dtype=torch.float64, device=dev).repeat(n_cells, 1, 1).contiguous()
+    out = torch.zeros((n_cells, 6), dtype=torch.float64, device=dev)
+    bad = [
+        (series.float(), Q, Q, out),
+        (series, Q.transpose(1, 2), Q, out),
+        (series, Q[:1].contiguous(), Q, out),
+        (series, Q, Q, out[:1].contiguous()),
+        (series[:, :, :5].contiguous(), Q, Q, out),
+        (series.cpu(), Q, Q, out),
+    ]
+    for args in bad:
+        with pytest.raises(rcell.RCellError) as e:
+            rcell.rcell_stress_reduce_static(*args)
+        assert e.value.name == "RC_EINVAL"
