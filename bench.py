@@ -1,21 +1,28 @@
 """Benchmark of the r-cell hot path on GB300.
 
-Workload (default): the copper bar -- an 8x2x2 hex mesh, one quadrature point
-per element = 32 r-cells of 10x10x10 FCC copper (4000 atoms each, a = 3.615 A)
-with Sutton-Chen EAM (n = 9, m = 6, eps = 1.2382e-2 eV, c = 39.432, a = 3.61 A,
-rc = 2a), Maxwell velocities at 300 K, Langevin damping 0.1 ps, dt = 2 fs.
-Uniaxial tension to 5 % in 25 increments, 1000 MD steps per increment with the
-stress averaged over the last 500.
+Workload (default, --workload necking_bar): the necking bar -- a 32x4x4 hex
+mesh with one quadrature point per element = 512 r-cells of 20 000
+Kremer-Grest beads each (400 chains of 50, melt density 0.85, T = 0.3,
+Langevin gamma = 0.5, dt = 0.005), 10.24 million beads on one GPU, with a 5 %
+cross-section imperfection at mid-length; uniaxial tension to 60 % in 150
+increments, 1000 MD steps per increment with the stress averaged over the last
+500.  The Verlet skin and the lanes per atom are chosen by the autotuner.
 
 One bench step = one FE load increment through the whole path: boundary
 conditions -> element F -> QR / box / remap -> 1000 MD steps (neighbour lists,
-density, forces, Verlet + Langevin, per-cell virial) -> time-averaged stress ->
-rotation and P -> FE internal force and explicit update.
+forces, Verlet + Langevin, per-cell virial) -> time-averaged stress -> rotation
+and P -> FE internal force and explicit update.  With --gpus N the 512 cells
+are split over the ranks (atom-balanced), every rank advances the same FE mesh
+and the stresses are all-gathered once per increment (strong scaling).
 
   value : atom-steps/s with everything resident in HBM (fe_step, device F).
-  e2e   : the same metric through the r-cell API with host buffers: each step
-          copies F from pinned host memory, runs the cells and copies sigma,
-          its standard error and P back (host<->device copies timed).
+  e2e   : the same increments through the public API with host buffers: the FE's
+          F copied to the host, handed to the r-cells from host memory, sigma,
+          its standard error and P copied back, P handed to the FE update from
+          host memory (the coupling of an FE code running on the host).
+
+Other workloads: copper_bar (32 Sutton-Chen cells), kg_bar (64 uneven KG
+cells), surrogate_fe, surrogate_train, kg_statics, kg_tensile.
 
 `--impl reference` times the FP64 CPU oracle on this machine's host cores on a
 bounded sample of the same workload (the reference arm of this benchmark).
@@ -176,6 +183,278 @@ def sc_algorithmic_flops_per_atom_step(rho):
     (density_per_atom, force_per_atom without sample, force_per_atom with sample)."""
     half_pairs = rho * 4.0 / 3.0 * np.pi * SC["rc"] ** 3 / 2.0
     return 14.0 * half_pairs, 42.0 * half_pairs + 40.0, 54.0 * half_pairs + 40.0
+
+
+NECK_MESH = (32, 4, 4)
+NECK_BEADS, NECK_CHAIN, NECK_DENSITY = 20000, 50, 0.85
+NECK_INC, NECK_STRAIN, NECK_MD, NECK_AVG = 150, 0.6, 1000, 500
+NECK_IMPERFECTION = 0.05
+NECK_WORKLOAD = "necking_bar_kg_512x20000"
+NECK_SKINS, NECK_TPAS = (0.3, 0.4, 0.5, 0.6), (1, 2)
+
+# DRAM bytes (read + write) per bead of one k_force<KG> launch (non-sampling
+# variant), from an ncu capture of the necking-bar cells at a smaller batch; a
+# launch's traffic grows in proportion to its beads (lists, positions and
+# velocities are per bead).  None until a capture of the current kernel exists.
+K_FORCE_KG_DRAM_BYTES_PER_ATOM = None
+K_FORCE_KG_SKIN = None  # the Verlet skin of that capture (the list length depends on it)
+
+
+def kg_algorithmic_flops_per_atom_step(rho, bonds_per_atom):
+    """Algorithmic FP32 work of one Kremer-Grest bead-step, counted once per
+    unordered pair inside rc (FMA = 2 FLOP): 26 FLOP per non-bonded LJ pair
+    (displacement 3, r^2 5, 1/r^2 1, r^-6 2, force scalar 3, f_i / f_j 12) plus
+    12 for its six virial components on the steps that record a stress sample,
+    40 per FENE + WCA bond, 40 per bead for the integrator and the Langevin
+    force.  Returns (without sample, with sample) per bead."""
+    half = rho * 4.0 / 3.0 * np.pi * 2.5 ** 3 / 2.0 - bonds_per_atom
+    return 26.0 * half + 40.0 * bonds_per_atom + 40.0, 38.0 * half + 40.0 * bonds_per_atom + 40.0
+
+
+def necking_cells(ne, n_distinct, procs, seed=5):
+    """The bar's r-cells (512 for the full mesh): n_distinct seeded 20 000-bead melts
+    (generated in a spawned process pool), each cell a copy shifted by a seeded
+    periodic translation."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(procs, n_distinct))) as pool:
+        return inputs.kg_cells(ne, NECK_BEADS // NECK_CHAIN, NECK_CHAIN, NECK_DENSITY, seed, n_distinct,
+                               starmap=pool.starmap)
+
+
+class CudaFE:
+    """The FE context behind the interface of dist.fe_step_sharded (device tensors)."""
+
+    def __init__(self, fe, ne, torch):
+        from paper_1902_09171_gb300 import rcell
+        self.rc, self.fe = rcell, fe
+        self.Fbuf = torch.zeros((ne, 3, 3), dtype=torch.float64, device="cuda")
+
+    def apply_bc(self, lam):
+        self.rc.fe_apply_bc(self.fe, lam)
+
+    def F(self):
+        self.rc.fe_get_F(self.fe, self.Fbuf)
+        return self.Fbuf
+
+    def update(self, P):
+        self.rc.fe_update(self.fe, P)
+
+
+def run_necking_bar(args):
+    import torch
+
+    from paper_1902_09171_gb300 import autotune, build, pipeline, rcell
+    from paper_1902_09171_gb300 import dist as rdist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    rcell.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    mesh = tuple(int(v) for v in args.mesh.split(",")) if args.mesh else NECK_MESH
+    ne = int(np.prod(mesh))
+    bounds = rdist.shard_by_atoms([NECK_BEADS] * ne, world)
+    a, b = bounds[rank]
+    t_prep = time.time()
+    cells = necking_cells(ne, args.distinct, args.procs)[a:b]
+    # soft start and equilibration of this rank's cells (input preparation)
+    ctx0, eq = pipeline.prepare_kg_batch(b - a, stream=stream, seed=7 + rank, soft_steps=args.soft_steps,
+                                         eq_steps=args.eq_steps, cells=cells)
+    rcell.rcell_destroy(ctx0)
+    # autotuned Verlet skin and lanes per atom, timed on 32 of this rank's cells
+    make = lambda skin: rcell.params_kg(seed=11 + rank, skin=skin)  # noqa: E731
+    if args.skin_kg > 0:
+        tuned, hit = {"skin": args.skin_kg, "tpa": args.tpa or 1, "table": []}, False
+    else:
+        tuned, hit = autotune.tune(make, eq[:32], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=100)
+    ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
+    rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
+    h = NECK_BEADS ** (1.0 / 3.0) / NECK_DENSITY ** (1.0 / 3.0)
+    X, conn = inputs.necking_mesh(*mesh, h, NECK_IMPERFECTION)
+    mask, val = inputs.uniaxial_bc(X, mesh[0] * h)
+    fe = rcell.fe_create(X, conn, mask, val, NECK_DENSITY, 2.0, 1.0, 1.0, stream=stream)
+    t_prep = time.time() - t_prep
+    md, navg = args.md_steps, min(NECK_AVG, args.md_steps // 2)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    P_local = torch.zeros((b - a, 3, 3), dtype=torch.float64, device="cuda")
+    cfe = CudaFE(fe, ne, torch)
+
+    def run_cells(F_local):
+        rcell.rcell_set_deformation(ctx, F_local)
+        rcell.rcell_run(ctx, md, navg)
+        rcell.rcell_stress(ctx, P=P_local)
+        return P_local
+
+    def lam_of(k):
+        return NECK_STRAIN * ((k % NECK_INC) + 1) / NECK_INC
+
+    def one_step(k):
+        if world == 1:
+            rcell.fe_step(fe, ctx, lam_of(k), md, navg, None)
+        else:
+            rdist.fe_step_sharded(cfe, run_cells, lam_of(k), bounds, rank)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    if rcell.rcell_sync(ctx) != 0:
+        raise RuntimeError("warm-up failed: " + rcell.rcell_last_error(ctx))
+    fp32_peak = rcell.rcell_fp32_peak(stream)
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rb0 = rcell.rcell_get_rebuilds(ctx)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[k][0].record(stream)
+            one_step(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    st = rcell.rcell_sync(ctx)
+    if st != 0:
+        raise RuntimeError("timed run failed: " + rcell.rcell_last_error(ctx))
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    rebuilds = float(np.mean(rcell.rcell_get_rebuilds(ctx) - rb0)) / args.steps
+    if world > 1:
+        ms = rdist_max(ms)
+        torch.distributed.barrier()
+    n_atoms_total = NECK_BEADS * ne
+    atom_steps = n_atoms_total * md * args.steps
+    value = atom_steps / (ms / 1e3)
+    launches_run = rcell.rcell_info(ctx)[2]
+    # deform + remap, stress, FE (bc, F, fint, update): fe_step; the sharded step
+    # launches the same kernels through the individual calls
+    launches_per_step = launches_run + 2 + 1 + 4
+
+    # ---- e2e: host F out of the FE and into the r-cells, host sigma / stderr / P back,
+    # host P into the FE update (the same kernels as fe_step, host copies timed) ----
+    pin = lambda shape: torch.zeros(shape, dtype=torch.float64).pin_memory()  # noqa: E731
+    F_h, sig_h, se_h = pin((ne, 3, 3)), pin((b - a, 6)), pin((b - a, 6))
+    P_h = pin((ne, 3, 3)) if world == 1 else pin((b - a, 3, 3))
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_ms = 0.0
+    k0 = args.warmup + args.steps
+    for k in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rcell.fe_apply_bc(fe, lam_of(k0 + k))
+        rcell.fe_get_F(fe, F_h)  # device -> host, synchronous
+        rcell.rcell_set_deformation(ctx, F_h[a:b])
+        rcell.rcell_run(ctx, md, navg)
+        rcell.rcell_stress(ctx, sig_h, se_h, P_h)  # device -> host, synchronous
+        if world == 1:
+            rcell.fe_update(fe, P_h)
+        else:
+            P_local.copy_(P_h, non_blocking=False)
+            rcell.fe_update(fe, rdist.gather_cells(P_local, bounds))
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        e2e_ms = rdist_max(e2e_ms)
+    e2e = n_atoms_total * md * e2e_steps / (e2e_ms / 1e3)
+    h2d = (b - a) * 72 + (ne if world == 1 else b - a) * 72
+    d2h = ne * 72 + (b - a) * (48 + 48 + 72)
+
+    # ---- per-kernel durations and the roofline of the dominant kernel ----
+    prof = rcell.rcell_profile_kernels(ctx, args.profile_steps)
+    Fe = np.zeros((ne, 3, 3))
+    rcell.fe_get_F(fe, Fe)
+    rho = NECK_DENSITY / float(np.mean(np.linalg.det(Fe)))
+    bpa = (NECK_CHAIN - 1) / NECK_CHAIN
+    f_ns, f_s = kg_algorithmic_flops_per_atom_step(rho, bpa)
+    n_ns, n_s = md - navg, navg
+    t_ns, t_s = prof["force"], prof.get("force_sample", prof["force"])
+    n_local = NECK_BEADS * (b - a)
+    achieved = (n_ns * f_ns + n_s * f_s) * n_local / ((n_ns * t_ns + n_s * t_s) / 1e3) / 1e12
+    traffic = (K_FORCE_KG_DRAM_BYTES_PER_ATOM * n_local
+               if (K_FORCE_KG_DRAM_BYTES_PER_ATOM is not None and tuned["skin"] == K_FORCE_KG_SKIN) else None)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
+                "kernel": "k_force<KG> (LJ + FENE/WCA forces, Verlet/Langevin, virial on sampling steps)",
+                "peak_source": "measured: FFMA probe on this GPU (rcell_fp32_peak), %.2f TFLOP/s; unit-count "
+                               "figure 152 SMs x 128 lanes x 2 FLOP x 2070 MHz = %.2f TFLOP/s"
+                               % (fp32_peak, fp32_unit_peak_tflops())}
+    Fxx = (float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max()))
+    rcell.fe_destroy(fe)
+    rcell.rcell_destroy(ctx)
+    out = None
+    if rank == 0:
+        out = {
+            "metric": "atom-steps/s batched r-cell MD (necking bar, %d Kremer-Grest r-cells x 20000 beads)" % ne,
+            "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+            "vs_baseline": None, "dtype": "f32 (pair math) / f64 (QR, remap, virial accumulation, FE)",
+            "data": "synthetic (seeded melts, GPU-equilibrated)",
+            "config": {"workload": NECK_WORKLOAD if mesh == NECK_MESH else "necking_bar_kg_%dx20000" % ne,
+                       "cells": ne, "atoms_per_cell": NECK_BEADS, "atoms": n_atoms_total, "mesh": list(mesh), "imperfection": NECK_IMPERFECTION,
+                       "increments_timed": [args.warmup + 1, args.warmup + args.steps], "of_increments": NECK_INC,
+                       "strain_per_increment": NECK_STRAIN / NECK_INC, "md_steps_per_increment": md, "n_avg": navg,
+                       "skin": tuned["skin"], "threads_per_atom": int(tuned["tpa"]),
+                       "autotune": "cache hit" if hit else ("fixed by --skin-kg" if args.skin_kg > 0 else "searched"),
+                       "distinct_melts": args.distinct, "l2": "flushed (256 MB write) between steps",
+                       "parallelism": f"cells split over {world} GPUs, P all-gathered" if world > 1 else "single GPU"},
+            "fe_load_steps_per_s": args.steps / (ms / 1e3),
+            "list_rebuilds_per_cell_per_increment": round(rebuilds, 2),
+            "element_F_xx_range": Fxx,
+            "e2e": {"value": e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "kernel_ms": {k: round(v, 5) for k, v in prof.items()},
+            "roofline": roofline,
+            "clocks": clk.summary(),
+            "prep_s": round(t_prep, 1),
+        }
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def rdist_max(v):
+    import torch
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def neck_oracle_sample(threads, md_steps):
+    """Time the FP64 oracle on a bounded sample of the necking bar: `threads` copies
+    of one of its 20 000-bead melts (host-generated, before the GPU's soft start),
+    md_steps MD steps each with the production parameters, one cell per host
+    thread.  Returns (atom_steps, seconds)."""
+    import concurrent.futures as cf
+
+    import oracle
+    x, H, bonds = inputs.kg_melt(NECK_BEADS // NECK_CHAIN, NECK_CHAIN, NECK_DENSITY, seed=5 * 1000)
+    x = inputs.to_f32(x)
+    pot = oracle.pot_kg()
+    mdp = oracle.MD(1, 1.0, 0.3, 2.0, 0.005, 11)
+    v = inputs.to_f32(inputs.maxwell(len(x), 1.0, 0.3, 1, 5))
+
+    def one(c):
+        oracle.md_run(pot, mdp, x, v, H, bonds=bonds, cell=c, ev=0, n_steps=md_steps, n_avg=md_steps)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(threads)))
+    return threads * NECK_BEADS * md_steps, time.perf_counter() - t0
+
+
+def neck_cpu_baseline(target_s=15.0):
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    a, t = neck_oracle_sample(1, 1)
+    steps = int(max(1, min(50, target_s / max(t, 1e-3))))
+    a, t = neck_oracle_sample(threads, steps)
+    return {"value": a / t, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{threads} copies of one 20000-bead necking-bar melt, {steps} MD steps each (production "
+                      f"parameters), one cell per host thread, FP64"}
 
 
 def run_ours(args):
@@ -365,6 +644,26 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
+    if args.workload == "necking_bar":
+        threads, md = cores, 2
+        for _ in range(args.warmup):
+            neck_oracle_sample(threads, 1)
+        tot_a, tot_t = 0, 0.0
+        for _ in range(args.steps):
+            a, t = neck_oracle_sample(threads, md)
+            tot_a += a
+            tot_t += t
+        value = tot_a / tot_t
+        return {"impl": "reference",
+                "metric": "atom-steps/s batched r-cell MD (necking bar, %d Kremer-Grest r-cells x 20000 beads)" % ne,
+                "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": NECK_WORKLOAD, "cells": int(np.prod(NECK_MESH)), "atoms_per_cell": NECK_BEADS},
+                "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+                                 "sample": f"each step: {threads} copies of one 20000-bead melt x {md} MD steps "
+                                           f"(FP64 oracle, one cell per host thread)"},
+                "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     threads = min(cores, MESH[0] * MESH[1] * MESH[2])
     md = 3
     for _ in range(args.warmup):
@@ -713,25 +1012,115 @@ def run_surrogate_fe(args):
                        "md_steps": NMD, "n_avg": NAVG, "members": K, "train_steps": args.train_steps}}
 
 
+def run_surrogate_fe_cu(args):
+    """The learned surrogate against plain r-cell MD on the copper bar: BASELINE's
+    training set of "config-2-style r-cells" read as the copper bar's own
+    Sutton-Chen r-cells (4000 atoms, 300 K).  Data: `--paths` cells driven along
+    seeded bar-like deformation histories (25 increments, --sur-md MD steps each,
+    stress averaged over the second half) through the batched r-cell engine;
+    BF16 training of a 4-member ensemble on 90 % of them; then the copper bar's
+    FE load history (8 x 2 x 2 hexahedra, 32 r-cells, 5 % in 25 increments) with
+    all-MD r-cells (fe_step) and with the surrogate + 2 % ensemble-spread MD
+    fallback (fe_step_surrogate: MD forced on the first 2 increments, trip above
+    2 %, release below 1 %, missed increments replayed on return).  Both bars
+    start from the same cells with the same Langevin seed; a third all-MD bar with
+    another seed states the MD noise of the axial stress curve."""
+    import torch
+
+    from paper_1902_09171_gb300 import build, pipeline, rcell
+    from paper_1902_09171_gb300 import surrogate as S
+    build.build()
+    rcell.load()
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    NP, T, K = args.paths, N_INC, 4
+    NMD = args.sur_md
+    NAVG = NMD // 2
+    t0 = time.time()
+    prm = rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=77)
+    ctx = rcell.rcell_create(prm, make_cells(NP, seed0=5000), stream=st)
+    F = inputs.bar_strain_paths(NP, T, seed=13)
+    U, Y, data_steps = pipeline.generate_dataset(ctx, F, NMD, NAVG, stream=st)
+    rcell.rcell_destroy(ctx)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    ntr = int(NP * 0.9)
+    sur = S.sur_create(K, max(NP, 32), T, seed=5, stream=st)
+    us, ys = pipeline.feature_scales(U[:ntr], Y[:ntr])
+    S.sur_set_scaling(sur, us, ys)
+    t0 = time.time()
+    pipeline.train(sur, U[:ntr].contiguous(), Y[:ntr].contiguous(), args.train_steps, lr=1e-3, n_members=K)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    s_floor = args.s_floor
+    err_ho, spread_q = pipeline.relative_error(sur, U[ntr:].contiguous(), Y[ntr:].contiguous(), K, s_floor=s_floor,
+                                               with_spread=True)
+    X, conn, mask, val = mesh("hex8")
+    ne = len(conn)
+    rho0, dt_fe, damp_fe, hg_fe = fe_params()
+    bars = []
+    for seed in (21, 21, 22):  # all-MD, surrogate (same cells, same seed), all-MD with another seed
+        c = rcell.rcell_create(rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=seed), make_cells(ne), stream=st)
+        bars.append((c, rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=st)))
+    lams = [STRAIN * (k + 1) / N_INC for k in range(N_INC)]
+    res = pipeline.fe_compare(bars[0][0], bars[1][0], sur, bars[0][1], bars[1][1], K, lams, NMD, NAVG,
+                              spread_on=0.02, spread_off=0.01, s_floor=s_floor, stream=st)
+    Fe = np.zeros((ne, 3, 3))
+    rcell.fe_get_F(bars[0][1], Fe)
+    noise = pipeline.fe_compare_md_only(bars[2][0], bars[2][1], lams, NMD, NAVG, stream=st)
+    a0, a2 = np.array(res["axial_md"]), np.array(noise["axial_md"])
+    md_noise = float(np.abs(a0 - a2).max() / max(np.abs(a0).max(), 1e-30))
+    for c, fe in bars:
+        rcell.fe_destroy(fe)
+        rcell.rcell_destroy(c)
+    S.sur_destroy(sur)
+    return {"metric": "FE load-steps/s, surrogate + MD fallback vs all-MD r-cells (copper bar)",
+            "value": len(lams) / (res["ms_sg"] / 1e3), "unit": "load-steps/s", "n_gpus": 1,
+            "all_md_value": len(lams) / (res["ms_md"] / 1e3), "speedup": res["ms_md"] / res["ms_sg"],
+            "max_rel_axial_stress_dev": res["max_rel_dev"], "md_noise_max_rel_axial_dev": md_noise,
+            "md_fraction": res["md_fraction"], "md_cell_increments": int(sum(res["n_md"])),
+            "all_md_cell_increments": ne * len(lams),
+            "heldout_rel_rms_error": err_ho, "heldout_spread_quantiles_10_50_90_99": spread_q,
+            "axial_md": res["axial_md"], "axial_sg": res["axial_sg"], "n_md_per_increment": res["n_md"],
+            "element_F_range": {"xx": [float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max())],
+                                "max_abs_shear": float(np.abs(Fe - np.diag(np.diag(Fe[0])) * 0 - np.eye(3))[:, [0, 0, 1, 2], [1, 2, 0, 0]].max())},
+            "data_atom_steps": data_steps, "data_s": t_data, "train_s": t_train, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"cu_surrogate_fe_8x2x2_{NP}_paths", "paths": NP, "increments": T,
+                       "md_steps": NMD, "n_avg": NAVG, "members": K, "train_steps": args.train_steps,
+                       "spread_on": 0.02, "spread_off": 0.01, "s_floor_gpa": s_floor}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="necking_bar",
+                    choices=["necking_bar", "copper_bar", "kg_bar", "surrogate_fe", "surrogate_fe_cu", "kg_statics",
+                             "surrogate_train", "kg_tensile"])
     ap.add_argument("--md-steps", type=int, default=MD_STEPS)
-    ap.add_argument("--skin", type=float, default=1.5)
+    ap.add_argument("--skin", type=float, default=1.5, help="copper bar: Verlet skin (A)")
+    ap.add_argument("--skin-kg", type=float, default=0.0, help="necking bar: fixed skin (0 = autotuned)")
     ap.add_argument("--element", default="hex8", choices=["hex8", "tet4"],
                     help="FE element of the copper bar: 8-node hexahedra (32 r-cells) or 4-node tetrahedra (192)")
     ap.add_argument("--tpa", type=int, default=0)
     ap.add_argument("--profile-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--distinct", type=int, default=16, help="necking bar: distinct seeded melts")
+    ap.add_argument("--mesh", default="", help="necking bar: another mesh nx,ny,nz (a smaller bar for profiling)")
+    ap.add_argument("--procs", type=int, default=16, help="host processes for the melts")
+    ap.add_argument("--soft-steps", type=int, default=1000)
+    ap.add_argument("--eq-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="copper_bar", choices=["copper_bar", "kg_bar", "surrogate_fe", "kg_statics", "surrogate_train", "kg_tensile"])
     ap.add_argument("--kg-cells", type=int, default=64)
     ap.add_argument("--pushoff", type=int, default=300)
     ap.add_argument("--paths", type=int, default=1024)
     ap.add_argument("--train-steps", type=int, default=2500)
+    ap.add_argument("--sur-md", type=int, default=400, help="copper surrogate: MD steps per increment")
+    ap.add_argument("--s-floor", type=float, default=0.5, help="copper surrogate: spread floor (GPa)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -740,10 +1129,16 @@ def main():
         if out is not None:
             print(json.dumps(out))
         return
+    if args.workload == "necking_bar":
+        out = run_necking_bar(args)
+        if out is not None:
+            if not args.no_cpu_baseline and out["n_gpus"] == 1:
+                out["cpu_baseline"] = neck_cpu_baseline(args.cpu_seconds)
+            print(json.dumps(out))
+        return
     if args.workload != "copper_bar":
-        if args.md_steps == MD_STEPS and args.workload == "kg_bar":
-            args.md_steps = 1000
-        run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "kg_statics": run_kg_statics,
+        run = {"kg_bar": run_kg_bar, "surrogate_fe": run_surrogate_fe, "surrogate_fe_cu": run_surrogate_fe_cu,
+               "kg_statics": run_kg_statics,
                "surrogate_train": run_surrogate_train, "kg_tensile": run_kg_tensile}[args.workload]
         out = run(args)
         print(json.dumps(out))

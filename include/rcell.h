@@ -367,6 +367,12 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
  * -- or exceeded it before and still exceed spread_off -- or all points when
  * force_md != 0, run n_steps of r-cell MD (rcell_set_active masks the rest) and
  * use its P; the others use P = J sigma_sur F^{-T}.  Then the FE update.
+ * While a point uses the surrogate its r-cell stays frozen in the state of its
+ * last MD increment, and the F of every increment it misses is recorded (up to
+ * RC_REPLAY_MAX; beyond that the first RC_REPLAY_MAX - 1 and the latest are
+ * kept).  When it returns to MD it first replays those increments one by one
+ * (deformation, n_steps of MD) before running this one, so that its r-cell
+ * follows the same per-increment deformation path as under all-MD (Eq. LAMMPS2).
  *   h_state  device, n_members x ne x 128 floats: recurrent states (zero to start)
  *   F_prev   device, ne x 9 doubles: F of the previous step (identity to start);
  *            overwritten with this step's F
@@ -374,12 +380,15 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
  *            because force_md was set (read for the hysteresis, which only
  *            keeps tripped points on MD; then overwritten)
  *   spread_out device, ne floats or NULL: the ensemble spread of every point
- *   n_md     host, may be NULL: number of points that ran MD
+ *   n_md     host, may be NULL: number of points that ran MD at this increment
+ *   n_replayed host, may be NULL: number of missed increments replayed (r-cell
+ *            MD runs of n_steps beyond the n_md of this increment)
  * fe, rc and sur must share one CUDA stream.  Synchronises once per step (to
  * skip the MD launches when no point needs them). */
+#define RC_REPLAY_MAX 32
 int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, struct sur_ctx *sur, double lambda, int n_steps, int n_avg,
                       float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
-                      int *md_flag, float *spread_out, int *n_md);
+                      int *md_flag, float *spread_out, int *n_md, int *n_replayed);
 
 /* First Piola-Kirchhoff stresses (ne x 9) used by the last FE update, into
  * `where` memory.  Synchronous when where == RC_HOST. */

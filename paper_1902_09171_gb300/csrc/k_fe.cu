@@ -155,6 +155,33 @@ __global__ void k_decide(const float *__restrict__ spread, float on, float off, 
     if (flag) atomicAdd(n_md, 1);
 }
 
+// Replay of missed increments: mask of the points that run MD at this increment
+// and still have a recorded deformation at replay position j.
+__global__ void k_replay_mask(const int *__restrict__ md_flag, const int *__restrict__ n_frozen, int j, int *mask,
+                              int ne) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    mask[e] = (md_flag[e] != 0 && n_frozen[e] > j) ? 1 : 0;
+}
+
+// After the step: a point on MD has no missed increment left; a point on the
+// surrogate records this increment's F at the next free position of its history
+// (when all kmax positions are taken, the last one is overwritten, so the
+// history keeps the first kmax - 1 missed increments and the latest).
+__global__ void k_track_frozen(const int *__restrict__ md_flag, const double *__restrict__ F, double *F_hist,
+                               int *n_frozen, int ne, int kmax) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    if (md_flag[e] != 0) {
+        n_frozen[e] = 0;
+        return;
+    }
+    const int n = n_frozen[e];
+    const int slot = n < kmax ? n : kmax - 1;
+    for (int k = 0; k < 9; k++) F_hist[((size_t)slot * ne + e) * 9 + k] = F[9 * e + k];
+    n_frozen[e] = n < kmax ? n + 1 : kmax;
+}
+
 // P = J sigma F^{-T} from the surrogate stress (FE frame) where the point is not on MD
 __global__ void k_merge_P(const int *__restrict__ md_flag, const float *__restrict__ s_sur, const double *__restrict__ F,
                           const double *__restrict__ P_md, double *P, int ne) {
@@ -201,6 +228,13 @@ void fe_launch_surrogate_merge(const int *md_flag, const float *s_sur, const dou
 void fe_launch_decide(const float *spread, float on, float off, int force_md, int *md_flag, int *n_md, int ne,
                       cudaStream_t s) {
     k_decide<<<(ne + 127) / 128, 128, 0, s>>>(spread, on, off, force_md, md_flag, n_md, ne);
+}
+void fe_launch_replay_mask(const int *md_flag, const int *n_frozen, int j, int *mask, int ne, cudaStream_t s) {
+    k_replay_mask<<<(ne + 127) / 128, 128, 0, s>>>(md_flag, n_frozen, j, mask, ne);
+}
+void fe_launch_track_frozen(const int *md_flag, const double *F, double *F_hist, int *n_frozen, int ne, int kmax,
+                            cudaStream_t s) {
+    k_track_frozen<<<(ne + 127) / 128, 128, 0, s>>>(md_flag, F, F_hist, n_frozen, ne, kmax);
 }
 void fe_launch_copy_F(const double *F, double *F_prev, int ne, cudaStream_t s) {
     k_copy_F<<<(9 * ne + 255) / 256, 256, 0, s>>>(F, F_prev, 9 * ne);

@@ -260,3 +260,6 @@ void fe_launch_surrogate_merge(const int *md_flag, const float *s_sur, const dou
 void fe_launch_decide(const float *spread, float on, float off, int force_md, int *md_flag, int *n_md, int ne,
                       cudaStream_t s);
 void fe_launch_copy_F(const double *F, double *F_prev, int ne, cudaStream_t s);
+void fe_launch_replay_mask(const int *md_flag, const int *n_frozen, int j, int *mask, int ne, cudaStream_t s);
+void fe_launch_track_frozen(const int *md_flag, const double *F, double *F_hist, int *n_frozen, int ne, int kmax,
+                            cudaStream_t s);

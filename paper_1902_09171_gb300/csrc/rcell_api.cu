@@ -79,6 +79,11 @@ struct fe_ctx {
     float *d_u = nullptr, *d_smean = nullptr, *d_spread = nullptr;
     double *d_Pmd = nullptr;
     int *d_nmd = nullptr;
+    // per point: deformation gradients of the increments missed while on the
+    // surrogate ([RC_REPLAY_MAX][ne][9]), their count, and a replay mask
+    double *d_Fhist = nullptr;
+    int *d_nfrozen = nullptr, *d_rmask = nullptr;
+    std::vector<int> h_flag, h_nfrozen;
     std::string err = "ok";
 };
 
@@ -1052,7 +1057,7 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
 
 int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, int n_steps, int n_avg,
                       float spread_on, float spread_off, float s_floor, int force_md, float *h_state, double *F_prev,
-                      int *md_flag, float *spread_out, int *n_md) {
+                      int *md_flag, float *spread_out, int *n_md, int *n_replayed) {
     if (!fe || !rc || !sur || !h_state || !F_prev || !md_flag) return RC_EINVAL;
     if (rc->n_cells != fe->ne) { fe->err = "one r-cell per element required"; return RC_EINVAL; }
     void *ss = nullptr;
@@ -1069,6 +1074,11 @@ int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, in
         CKF(fe, dalloc(fe->allocs, &fe->d_spread, ne));
         CKF(fe, dalloc(fe->allocs, &fe->d_Pmd, 9 * (size_t)ne));
         CKF(fe, dalloc(fe->allocs, &fe->d_nmd, 1));
+        CKF(fe, dalloc(fe->allocs, &fe->d_Fhist, (size_t)RC_REPLAY_MAX * ne * 9));
+        CKF(fe, dalloc(fe->allocs, &fe->d_nfrozen, ne));
+        CKF(fe, dalloc(fe->allocs, &fe->d_rmask, ne));
+        fe->h_flag.assign(ne, 0);
+        fe->h_nfrozen.assign(ne, 0);
     }
     int e;
     // 1. boundary conditions and element F
@@ -1084,22 +1094,42 @@ int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, in
         CKF(fe, cudaMemcpyAsync(spread_out, fe->d_spread, sizeof(float) * ne, cudaMemcpyDeviceToDevice, st));
     int nmd = 0;
     CKF(fe, cudaMemcpyAsync(&nmd, fe->d_nmd, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKF(fe, cudaMemcpyAsync(fe->h_flag.data(), md_flag, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+    CKF(fe, cudaMemcpyAsync(fe->h_nfrozen.data(), fe->d_nfrozen, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
     CKF(fe, cudaStreamSynchronize(st));
-    // 4. MD for the flagged points only (the others keep their frozen r-cell state;
-    //    a point that returns to MD takes the whole deformation since its last MD
-    //    increment in one remap)
+    // 4. a point returning to MD resumes from its frozen r-cell state (the state of
+    //    its last MD increment) and first replays, increment by increment, the
+    //    deformations it missed on the surrogate (R15); points replay side by side,
+    //    each masked out once its own history is used up
+    int max_k = 0, replayed = 0;
+    for (int e = 0; e < ne; e++)
+        if (fe->h_flag[e] != 0) {
+            max_k = std::max(max_k, fe->h_nfrozen[e]);
+            replayed += fe->h_nfrozen[e];
+        }
+    for (int j = 0; j < max_k; j++) {
+        fe_launch_replay_mask(md_flag, fe->d_nfrozen, j, fe->d_rmask, ne, st);
+        if ((e = rcell_set_active(rc, fe->d_rmask, RC_DEVICE)) != RC_OK) return e;
+        if ((e = rcell_set_deformation(rc, fe->d_Fhist + (size_t)j * ne * 9, RC_DEVICE)) != RC_OK) return e;
+        if ((e = rcell_run(rc, n_steps, n_avg)) != RC_OK) return e;  // the all-MD kernel sequence
+    }
+    // 5. MD for the flagged points at this increment (the others keep their frozen
+    //    r-cell state)
     if (nmd > 0) {
         if ((e = rcell_set_active(rc, md_flag, RC_DEVICE)) != RC_OK) return e;
         if ((e = rcell_set_deformation(rc, fe->d_F, RC_DEVICE)) != RC_OK) return e;
         if ((e = rcell_run(rc, n_steps, n_avg)) != RC_OK) return e;
         if ((e = rcell_stress(rc, nullptr, nullptr, fe->d_Pmd, RC_DEVICE)) != RC_OK) return e;
     }
-    // 5. merge: MD P where flagged, J sigma_sur F^-T elsewhere; then the FE update
+    // 6. merge: MD P where flagged, J sigma_sur F^-T elsewhere; record the missed
+    //    increment of every surrogate point; then the FE update
     fe_launch_surrogate_merge(md_flag, fe->d_smean, fe->d_F, fe->d_Pmd, fe->d_P, ne, st);
+    fe_launch_track_frozen(md_flag, fe->d_F, fe->d_Fhist, fe->d_nfrozen, ne, RC_REPLAY_MAX, st);
     fe_launch_copy_F(fe->d_F, F_prev, ne, st);
     CKF(fe, cudaGetLastError());
     if ((e = fe_update(fe, fe->d_P, RC_DEVICE)) != RC_OK) return e;
     if (n_md) *n_md = nmd;
+    if (n_replayed) *n_replayed = replayed;
     return RC_OK;
 }
 

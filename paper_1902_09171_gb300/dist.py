@@ -54,3 +54,28 @@ def max_over_ranks(value: float, group=None) -> float:
     t = torch.tensor([value], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def fe_step_sharded(fe, run_cells, lam: float, bounds, rank: int, group=None):
+    """One FE load increment with the r-cells split over ranks: the FEM <-> r-cell
+    scatter / gather of Sec. 2.3 in GPU form.  Every rank holds the whole (small)
+    FE mesh and advances it identically; rank `rank` runs only its own cells
+    bounds[rank] = (a, b):
+      1. fe.apply_bc(lam); F = fe.F()          all elements, on every rank
+      2. P_local = run_cells(F[a:b])           this rank's r-cells (QR, remap, MD, stress)
+      3. P = all-gather of P_local             the only exchange: 9 doubles per cell
+      4. fe.update(P)                          on every rank, from the same P
+    fe: object with apply_bc(lam), F() -> tensor (ne, 3, 3) and update(P);
+    run_cells(F_local) -> tensor (b - a, 3, 3).  Without an initialised process
+    group (one rank) step 3 is the identity.  Returns the full P."""
+    import torch.distributed as dist
+    fe.apply_bc(lam)
+    F = fe.F()
+    a, b = bounds[rank]
+    P_local = run_cells(F[a:b].contiguous())
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        P = gather_cells(P_local, bounds, group)
+    else:
+        P = P_local
+    fe.update(P)
+    return P

@@ -94,6 +94,18 @@ def tet_mesh(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float):
     return X, np.asarray(conn, dtype=np.int32)
 
 
+def necking_mesh(nx: int, ny: int, nz: int, h: float, imperfection: float = 0.05):
+    """Hex-8 bar of nx x ny x nz cubic elements of edge h along x, with a cross-section
+    imperfection at mid-length: the nodes of the plane x = (nx // 2) h are moved
+    towards the bar axis by the factor sqrt(1 - imperfection) in y and z, so that
+    the section there has (1 - imperfection) of the nominal area.  Returns X, conn."""
+    X, conn = hex_mesh(nx, ny, nz, nx * h, ny * h, nz * h)
+    mid = np.abs(X[:, 0] - (nx // 2) * h) < 1e-9 * h
+    c = np.array([0.5 * ny * h, 0.5 * nz * h])
+    X[mid, 1:] = c + np.sqrt(1.0 - imperfection) * (X[mid, 1:] - c)
+    return X, conn
+
+
 def uniaxial_bc(X: np.ndarray, L: float, all_nodes: bool = False):
     """Boundary conditions for uniaxial extension along x (load factor = engineering strain).
 
@@ -165,43 +177,30 @@ def kg_melt(n_chains: int, chain_len: int, density: float, seed: int, bond: floa
 
 def _pushoff(x, L, bonds, chain_len, iters, rcut=0.95, cap=0.05):
     """Capped gradient steps on sum over non-bonded pairs of (rcut - r)^2 (r < rcut) plus
-    (r - bond)^2 springs on bonds; a cubic-box cell list in NumPy."""
+    (r - bond)^2 springs on bonds; the close pairs come from a periodic k-d tree."""
+    from scipy.spatial import cKDTree
+
     n = x.shape[0]
-    nb = max(1, int(L // 1.0))
-    w = L / nb
     bi, bj = bonds[:, 0], bonds[:, 1]
     for _ in range(iters):
         x = np.mod(x, L)
-        cid = np.minimum((x // w).astype(np.int64), nb - 1)
-        key = (cid[:, 0] * nb + cid[:, 1]) * nb + cid[:, 2]
-        order = np.argsort(key, kind="stable")
-        skey = key[order]
-        starts = np.searchsorted(skey, np.arange(nb ** 3))
-        ends = np.searchsorted(skey, np.arange(nb ** 3), side="right")
+        x[x >= L] -= L  # np.mod can round up to L
+        pairs = cKDTree(x, boxsize=L).query_pairs(rcut, output_type="ndarray")
         disp = np.zeros_like(x)
         worst = 0.0
-        offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
-        for (a, b, c) in offs:
-            nc = (cid + np.array([a, b, c])) % nb
-            nkey = (nc[:, 0] * nb + nc[:, 1]) * nb + nc[:, 2]
-            s, e = starts[nkey], ends[nkey]
-            cnt = e - s
-            mx = int(cnt.max()) if n else 0
-            for t in range(mx):
-                has = cnt > t
-                ii = np.nonzero(has)[0]
-                jj = order[s[ii] + t]
-                keep = jj != ii
-                same_chain_adjacent = (ii // chain_len == jj // chain_len) & (np.abs(ii - jj) == 1)
-                keep &= ~same_chain_adjacent
-                ii, jj = ii[keep], jj[keep]
-                d = x[ii] - x[jj]
-                d -= L * np.round(d / L)
-                r = np.linalg.norm(d, axis=1)
-                m = (r < rcut) & (r > 1e-12)
-                if np.any(m):
-                    worst = max(worst, float((rcut - r[m]).max()))
-                    np.add.at(disp, ii[m], (0.5 * (rcut - r[m]) / r[m])[:, None] * d[m])
+        if len(pairs):
+            ii, jj = pairs[:, 0], pairs[:, 1]
+            adjacent = (ii // chain_len == jj // chain_len) & (np.abs(ii - jj) == 1)
+            ii, jj = ii[~adjacent], jj[~adjacent]
+            d = x[ii] - x[jj]
+            d -= L * np.round(d / L)
+            r = np.linalg.norm(d, axis=1)
+            m = (r < rcut) & (r > 1e-12)
+            if np.any(m):
+                worst = float((rcut - r[m]).max())
+                push = (0.5 * (rcut - r[m]) / r[m])[:, None] * d[m]
+                np.add.at(disp, ii[m], push)
+                np.add.at(disp, jj[m], -push)
         d = x[bj] - x[bi]
         d -= L * np.round(d / L)
         r = np.linalg.norm(d, axis=1)
@@ -252,12 +251,42 @@ def strain_paths(n_paths: int, n_inc: int, seed: int, max_strain: float = 0.3, m
     return F
 
 
-def kg_cells(n_cells: int, n_chains: int, chain_len: int, density: float, seed: int, n_distinct: int = 4):
+def bar_strain_paths(n_paths: int, n_inc: int, seed: int, max_axial: float = 0.15, max_shear: float = 0.12,
+                     max_lateral: float = 0.05, jitter: float = 0.005):
+    """Seeded deformation-gradient histories F[p, t] (t = 0..n_inc, F[:, 0] = I) of the
+    kind the elements of a bar in uniaxial tension go through: a monotone axial
+    stretch to an amplitude in [-max_axial / 5, max_axial] along a ramp t^q
+    (q in [0.5, 2]); lateral stretches -nu eps_x (nu in [0, 0.5]) plus their own
+    ramp in [-max_lateral, max_lateral / 4]; the four shears F_xy, F_xz, F_yx, F_zx
+    each ramped to an amplitude in [-max_shear, max_shear]; a random ramp of
+    amplitude `jitter` in all nine components.  Returns (n_paths, n_inc + 1, 3, 3)."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(n_inc + 1) / n_inc
+    F = np.tile(np.eye(3), (n_paths, n_inc + 1, 1, 1))
+    for p in range(n_paths):
+        ex = rng.uniform(-0.2 * max_axial, max_axial) * t ** rng.uniform(0.5, 2.0)
+        nu = rng.uniform(0.0, 0.5)
+        F[p, :, 0, 0] = 1.0 + ex
+        for d in (1, 2):
+            F[p, :, d, d] = 1.0 - nu * ex + rng.uniform(-max_lateral, 0.25 * max_lateral) * t ** rng.uniform(0.5, 2.0)
+        for (i, j) in ((0, 1), (0, 2), (1, 0), (2, 0)):
+            F[p, :, i, j] = rng.uniform(-max_shear, max_shear) * t ** rng.uniform(0.5, 2.0)
+        F[p] += jitter * rng.uniform(-1, 1, (3, 3))[None] * t[:, None, None]
+    return F
+
+
+def kg_cells(n_cells: int, n_chains: int, chain_len: int, density: float, seed: int, n_distinct: int = 4,
+             starmap=None):
     """n_cells Kremer-Grest r-cells built from n_distinct seeded melts, each copy
     shifted by a seeded random periodic translation (positions wrapped).  Returns
-    a list of dicts (H0, x0, bonds)."""
+    a list of dicts (H0, x0, bonds).  starmap (e.g. a process pool's) generates
+    the melts in parallel; the result does not depend on it."""
     rng = np.random.default_rng(seed)
-    melts = [kg_melt(n_chains, chain_len, density, seed=seed * 1000 + k) for k in range(n_distinct)]
+    jobs = [(n_chains, chain_len, density, seed * 1000 + k) for k in range(n_distinct)]
+    if starmap is None:
+        melts = [kg_melt(*j) for j in jobs]
+    else:
+        melts = list(starmap(kg_melt, jobs))
     cells = []
     for c in range(n_cells):
         x, H, b = melts[c % n_distinct]

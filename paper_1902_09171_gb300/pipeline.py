@@ -29,11 +29,13 @@ def _torch():
 
 
 def prepare_kg_batch(n_cells, n_chains=100, chain_len=50, density=0.85, seed=3, stream=None, soft_steps=2000,
-                     eq_steps=2000, kT=0.3, skin=0.3, n_distinct=4, tpa=1):
+                     eq_steps=2000, kT=0.3, skin=0.3, n_distinct=4, tpa=1, cells=None, starmap=None):
     """Melts -> soft start (dt 0.002, strong friction, T = 1, displacement limited to
     0.02 sigma per step) -> equilibration at the production temperature.  Returns (ctx, cells) with ctx holding the equilibrated
-    production batch (dt = 0.005, gamma = 0.5)."""
-    cells = inputs.kg_cells(n_cells, n_chains, chain_len, density, seed, n_distinct)
+    production batch (dt = 0.005, gamma = 0.5).  cells: prebuilt melts (dicts of
+    inputs.kg_cells) instead of generating them; starmap: parallel melt generation."""
+    if cells is None:
+        cells = inputs.kg_cells(n_cells, n_chains, chain_len, density, seed, n_distinct, starmap=starmap)
     soft = rcell.params_kg(tau=0.5, kT=1.0, dt=0.002, seed=seed, skin=skin, max_step=0.02)
     ctx = rcell.rcell_create(soft, cells, stream=stream)
     rcell.rcell_set_tuning(ctx, tpa, 1)
@@ -147,8 +149,9 @@ def fe_compare_surrogate_only(ctx_sg, sur, fe_sg, n_members, lambdas, n_steps, n
     P_sg, n_md = [], []
     e0.record(st)
     for k, lam in enumerate(lambdas):
-        n_md.append(rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
-                                            k < md_first, h, Fp, flag))
+        n, r = rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
+                                       k < md_first, h, Fp, flag, with_replays=True)
+        n_md.append(n + r)  # MD cell-increments: this increment's and the replayed ones
         rcell.fe_get_P(fe_sg, P)
         P_sg.append(P[:, 0, 0].mean())
     e1.record(st)
@@ -189,8 +192,9 @@ def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n
     P_sg, sp = [], []
     e0.record(st)
     for k, lam in enumerate(lambdas):
-        n = rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
-                                    k < md_first, h, Fp, flag, spread)
+        n, r = rcell.fe_step_surrogate(fe_sg, ctx_sg, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor,
+                                       k < md_first, h, Fp, flag, spread, with_replays=True)
+        n += r  # MD cell-increments: this increment's and the replayed ones
         rcell.fe_get_P(fe_sg, P)
         P_sg.append(P[:, 0, 0].mean())
         sp.append(spread.median())
@@ -204,6 +208,25 @@ def fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, n_members, lambdas, n_steps, n
     res["max_rel_dev"] = float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30))
     res["md_fraction"] = float(sum(res["n_md"]) / (ne * len(lambdas)))
     return res
+
+
+def fe_compare_md_only(ctx, fe, lambdas, n_steps, n_avg, stream=None):
+    """The all-MD half of fe_compare on its own (another bar, e.g. another Langevin
+    seed, to state the MD noise of the axial stress curve)."""
+    torch = _torch()
+    ne = rcell.rcell_info(ctx)[0]
+    st = stream or torch.cuda.current_stream()
+    P = torch.zeros((ne, 3, 3), dtype=torch.float64, device=torch.device("cuda"))
+    out = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for lam in lambdas:
+        rcell.fe_step(fe, ctx, lam, n_steps, n_avg, None)
+        rcell.fe_get_P(fe, P)
+        out.append(P[:, 0, 0].mean())
+    e1.record(st)
+    torch.cuda.synchronize()
+    return {"ms_md": e0.elapsed_time(e1), "axial_md": [float(v) for v in out]}
 
 
 def tensile_F(eps, nu=0.5):

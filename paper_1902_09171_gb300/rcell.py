@@ -99,7 +99,7 @@ def load(path: str | None = None):
         "fe_update": ([vp, vp, C.c_int], C.c_int),
         "fe_step": ([vp, vp, C.c_double, C.c_int, C.c_int, vp], C.c_int),
         "fe_step_surrogate": ([vp, vp, vp, C.c_double, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, C.c_int,
-                               vp, vp, vp, vp, C.POINTER(C.c_int)], C.c_int),
+                               vp, vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "fe_get_P": ([vp, vp, C.c_int], C.c_int),
         "fe_get_state": ([vp, vp, vp], C.c_int),
         "fe_destroy": ([vp], None),
@@ -434,15 +434,16 @@ def fe_step(fe, rc, lam: float, n_steps: int, n_avg: int, u_out=None):
 
 
 def fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, force_md, h_state, F_prev,
-                      md_flag, spread_out=None):
+                      md_flag, spread_out=None, with_replays=False):
     """Device state tensors: h_state (float32, members x ne x 128), F_prev (float64,
     ne x 3 x 3), md_flag (int32, ne), optional spread_out (float32, ne).
-    Returns the number of points that ran MD."""
-    n = C.c_int(0)
+    Returns the number of points that ran MD at this increment, or with
+    with_replays=True the pair (that number, missed increments replayed)."""
+    n, r = C.c_int(0), C.c_int(0)
     ptr = [None if t is None else C.c_void_p(t.data_ptr()) for t in (h_state, F_prev, md_flag, spread_out)]
     _check(load().fe_step_surrogate(fe, rc, sur, lam, n_steps, n_avg, spread_on, spread_off, s_floor, int(force_md),
-                                    ptr[0], ptr[1], ptr[2], ptr[3], C.byref(n)), rc, "fe_step_surrogate")
-    return n.value
+                                    ptr[0], ptr[1], ptr[2], ptr[3], C.byref(n), C.byref(r)), rc, "fe_step_surrogate")
+    return (n.value, r.value) if with_replays else n.value
 
 
 def fe_get_P(fe, P):

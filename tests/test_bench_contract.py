@@ -23,7 +23,7 @@ def test_reference_arm_prints_one_contract_line():
         assert k in out, k
     assert out["value"] > 0 and out["ms_per_step"] > 0 and out["higher_is_better"] is True
     assert out["steps"] == 1 and out["warmup"] >= 3 and out["n_gpus"] == 1
-    assert out["config"]["workload"] == "copper_bar_sc_eam_32x4000"
+    assert out["config"]["workload"] == "necking_bar_kg_512x20000"  # the default workload
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == out["value"] and cb["sample"]
     e2e = out["e2e"]

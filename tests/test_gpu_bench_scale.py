@@ -48,10 +48,13 @@ def torch():
 
 def copper_bar_cells(jit):
     """The benchmark's r-cells: 10x10x10 FCC copper (a = 3.615 A), Maxwell 300 K per
-    cell (seed 1000 + c), positions jittered by up to `jit` A (seed 500 + c)."""
+    cell (seed 1000 + c), positions jittered by up to `jit` A (seed 500 + c) and
+    wrapped into the box on the host, so that the engine's own wrap moves no atom
+    (an FP32 wrap would shift a coordinate by up to half an ulp of the box length)."""
     x, H = inputs.fcc(10, 10, 10, 3.615)
     kT = 300 * KB
-    return [dict(H0=H, x0=inputs.to_f32(inputs.jitter(x, jit, 500 + c)),
+    L = H[0, 0]
+    return [dict(H0=H, x0=inputs.to_f32(np.mod(inputs.jitter(x, jit, 500 + c), L)),
                  v0=inputs.to_f32(inputs.maxwell(len(x), M_CU, kT, 0, 1000 + c))) for c in range(N_BAR)]
 
 
@@ -149,7 +152,11 @@ def test_kremer_grest_chunked_tensile_trajectory_matches_oracle(torch):
     # contraction, FENE + WCA bonds and the non-bonded LJ, same Philox stream
     prm = rcell.params_kg(kT=0.1, seed=8)
     x0, H0, bonds = inputs.kg_melt(20, 50, 0.85, seed=12, pushoff_iters=300)
-    x0 = inputs.to_f32(x0)
+    # a pushed-off melt still holds near-overlaps whose forces would stretch bonds
+    # past R0 within a few steps: relax it first (host side, the oracle's FIRE)
+    x0, _ = oracle.fire_minimize(oracle_pot(prm), x0, H0, 1.0, 1.0, 0.001, 0.01, 2000, bonds=bonds, units=1,
+                                 dmax=0.05)
+    x0 = inputs.to_f32(np.mod(x0, H0[0, 0]))
     v0 = inputs.to_f32(inputs.maxwell(len(x0), 1.0, 0.1, 1, 12))
     cell = dict(H0=H0, x0=x0, v0=v0, bonds=bonds)
     n = len(x0)
