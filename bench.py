@@ -221,6 +221,13 @@ def necking_cells(ne, n_distinct, procs, seed=5):
                                starmap=pool.starmap)
 
 
+def axial_predictor(X):
+    """Affine predictor of a uniaxial load increment along x: g = (X_x, 0, 0)."""
+    g = np.zeros_like(X)
+    g[:, 0] = X[:, 0]
+    return g
+
+
 class CudaFE:
     """The FE context behind the interface of dist.fe_step_sharded (device tensors)."""
 
@@ -277,6 +284,7 @@ def run_necking_bar(args):
     X, conn = inputs.necking_mesh(*mesh, h, NECK_IMPERFECTION)
     mask, val = inputs.uniaxial_bc(X, mesh[0] * h)
     fe = rcell.fe_create(X, conn, mask, val, NECK_DENSITY, 2.0, 1.0, 1.0, stream=stream)
+    rcell.fe_set_predictor(fe, axial_predictor(X))
     t_prep = time.time() - t_prep
     md, navg = args.md_steps, min(NECK_AVG, args.md_steps // 2)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -398,6 +406,7 @@ def run_necking_bar(args):
                        "skin": tuned["skin"], "threads_per_atom": int(tuned["tpa"]),
                        "autotune": "cache hit" if hit else ("fixed by --skin-kg" if args.skin_kg > 0 else "searched"),
                        "distinct_melts": args.distinct, "l2": "flushed (256 MB write) between steps",
+                       "fe_predictor": "affine, g = (X_x, 0, 0)",
                        "parallelism": f"cells split over {world} GPUs, P all-gathered" if world > 1 else "single GPU"},
             "fe_load_steps_per_s": args.steps / (ms / 1e3),
             "list_rebuilds_per_cell_per_increment": round(rebuilds, 2),
@@ -720,8 +729,12 @@ def run_kg_bar(args):
         x, v, _ = rcell.rcell_get_atoms(ctx, k, len(c["x0"]))
         eq.append(dict(H0=c["H0"], x0=x, v0=v, bonds=c["bonds"]))
     rcell.rcell_destroy(ctx)
-    ctx = rcell.rcell_create(rcell.params_kg(), eq, stream=stream)
-    rcell.rcell_set_tuning(ctx, args.tpa or 1, 1)
+    # autotuned Verlet skin and lanes per atom (timed on the bar's own cells)
+    from paper_1902_09171_gb300 import autotune
+    make = lambda skin: rcell.params_kg(skin=skin)  # noqa: E731
+    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=100)
+    ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
+    rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     rcell.rcell_run(ctx, 2000, 0)
     st = rcell.rcell_sync(ctx)
     if st != 0:
@@ -756,7 +769,9 @@ def run_kg_bar(args):
            "value": n_atoms * md * args.steps / (ms / 1e3), "unit": "atom-steps/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "status": rcell.STATUS[st], "data": "synthetic",
-           "config": {"workload": f"kg_bar_{len(cells)}_cells_5k_20k", "atoms": n_atoms, "md_steps": md},
+           "config": {"workload": f"kg_bar_{len(cells)}_cells_5k_20k", "atoms": n_atoms, "md_steps": md,
+                      "skin": tuned["skin"], "threads_per_atom": int(tuned["tpa"]),
+                      "autotune": "cache hit" if hit else "searched", "autotune_table": tuned.get("table")},
            "fe_load_steps_per_s": args.steps / (ms / 1e3),
            "element_F_xx_range": [float(Fe[:, 0, 0].min()), float(Fe[:, 0, 0].max())],
            "list_rebuilds_per_cell_per_increment": round(float(np.mean(rebuilds)), 2),
@@ -988,23 +1003,32 @@ def run_surrogate_fe(args):
                                                with_spread=True)
     ne = 32
     ctx_md, cells = pipeline.prepare_kg_batch(ne, stream=st, seed=21)
+    # the surrogate bar starts from the same states with the same Langevin seed as the
+    # all-MD bar (prepare_kg_batch's production seed is seed + 1); a third all-MD bar
+    # with another seed states the MD noise of the axial stress curve
     ctx_sg = rcell.rcell_create(rcell.params_kg(seed=22), cells, stream=st)
+    ctx_nz = rcell.rcell_create(rcell.params_kg(seed=99), cells, stream=st)
     L = cells[0]["H0"][0, 0]
     X, conn = inputs.hex_mesh(8, 2, 2, 8 * L, 2 * L, 2 * L)
     mask, val = inputs.uniaxial_bc(X, 8 * L)
     fe_md = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=st)
     fe_sg = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=st)
+    fe_nz = rcell.fe_create(X, conn, mask, val, 0.85, 2.0, 1.0, 1.0, stream=st)
     lams = [0.3 * (k + 1) / 60 for k in range(60)]
     res = pipeline.fe_compare(ctx_md, ctx_sg, sur, fe_md, fe_sg, K, lams, NMD, NAVG, s_floor=0.2, stream=st)
-    for h in (fe_md, fe_sg):
+    nz = pipeline.fe_compare_md_only(ctx_nz, fe_nz, lams, NMD, NAVG, stream=st)
+    a0, a2 = np.array(res["axial_md"]), np.array(nz["axial_md"])
+    md_noise = float(np.abs(a0 - a2).max() / max(np.abs(a0).max(), 1e-30))
+    for h in (fe_md, fe_sg, fe_nz):
         rcell.fe_destroy(h)
-    rcell.rcell_destroy(ctx_md)
-    rcell.rcell_destroy(ctx_sg)
+    for c in (ctx_md, ctx_sg, ctx_nz):
+        rcell.rcell_destroy(c)
     S.sur_destroy(sur)
     return {"metric": "FE load-steps/s, surrogate + MD fallback vs all-MD r-cells",
             "value": len(lams) / (res["ms_sg"] / 1e3), "unit": "load-steps/s", "n_gpus": 1,
             "all_md_value": len(lams) / (res["ms_md"] / 1e3), "speedup": res["ms_md"] / res["ms_sg"],
-            "max_rel_axial_stress_dev": res["max_rel_dev"], "md_fraction": res["md_fraction"],
+            "max_rel_axial_stress_dev": res["max_rel_dev"], "md_noise_max_rel_axial_dev": md_noise,
+            "md_fraction": res["md_fraction"],
             "heldout_rel_rms_error": err_ho, "heldout_spread_quantiles_10_50_90_99": spread_q,
             "data_atom_steps": data_steps, "data_s": t_data, "train_s": t_train, "higher_is_better": True,
             "data": "synthetic",
@@ -1019,7 +1043,8 @@ def run_surrogate_fe_cu(args):
     seeded bar-like deformation histories (25 increments, --sur-md MD steps each,
     stress averaged over the second half) through the batched r-cell engine;
     BF16 training of a 4-member ensemble on 90 % of them; then the copper bar's
-    FE load history (8 x 2 x 2 hexahedra, 32 r-cells, 5 % in 25 increments) with
+    FE load history (8 x 2 x 2 hexahedra, 32 r-cells, 5 % in 25 increments, affine
+    load predictor) with
     all-MD r-cells (fe_step) and with the surrogate + 2 % ensemble-spread MD
     fallback (fe_step_surrogate: MD forced on the first 2 increments, trip above
     2 %, release below 1 %, missed increments replayed on return).  Both bars
@@ -1039,7 +1064,7 @@ def run_surrogate_fe_cu(args):
     t0 = time.time()
     prm = rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=77)
     ctx = rcell.rcell_create(prm, make_cells(NP, seed0=5000), stream=st)
-    F = inputs.bar_strain_paths(NP, T, seed=13)
+    F = inputs.bar_strain_paths(NP, T, seed=13, max_axial=0.08, max_shear=0.02, max_lateral=0.03)
     U, Y, data_steps = pipeline.generate_dataset(ctx, F, NMD, NAVG, stream=st)
     rcell.rcell_destroy(ctx)
     torch.cuda.synchronize()
@@ -1061,7 +1086,9 @@ def run_surrogate_fe_cu(args):
     bars = []
     for seed in (21, 21, 22):  # all-MD, surrogate (same cells, same seed), all-MD with another seed
         c = rcell.rcell_create(rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=seed), make_cells(ne), stream=st)
-        bars.append((c, rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=st)))
+        fe = rcell.fe_create(X, conn, mask, val, rho0, dt_fe, damp_fe, hg_fe, stream=st)
+        rcell.fe_set_predictor(fe, axial_predictor(X))
+        bars.append((c, fe))
     lams = [STRAIN * (k + 1) / N_INC for k in range(N_INC)]
     res = pipeline.fe_compare(bars[0][0], bars[1][0], sur, bars[0][1], bars[1][1], K, lams, NMD, NAVG,
                               spread_on=0.02, spread_off=0.01, s_floor=s_floor, stream=st)
@@ -1088,7 +1115,8 @@ def run_surrogate_fe_cu(args):
             "data": "synthetic",
             "config": {"workload": f"cu_surrogate_fe_8x2x2_{NP}_paths", "paths": NP, "increments": T,
                        "md_steps": NMD, "n_avg": NAVG, "members": K, "train_steps": args.train_steps,
-                       "spread_on": 0.02, "spread_off": 0.01, "s_floor_gpa": s_floor}}
+                       "spread_on": 0.02, "spread_off": 0.01, "s_floor_gpa": s_floor,
+                       "fe_predictor": "affine, g = (X_x, 0, 0)"}}
 
 
 def main():

@@ -340,8 +340,23 @@ int fe_create(const double *X, int nn, const int *hex, int ne, const int *bc_mas
 int fe_create_tet4(const double *X, int nn, const int *tet, int ne, const int *bc_mask, const double *bc_val,
                    double rho0, double dt, double damping, void *stream, fe_ctx **out);
 
-/* Set the prescribed DOFs to lambda * bc_val.  Asynchronous. */
+/* Set the prescribed DOFs to lambda * bc_val.  With a predictor (fe_set_predictor)
+ * every free DOF first moves by (lambda - lambda_prev) g, lambda_prev being the
+ * load factor of the previous call on this context (0 at creation).
+ * Asynchronous. */
 int fe_apply_bc(fe_ctx *fe, double lambda);
+
+/* Affine predictor of the load increment, with no counterpart in the paper's
+ * explicit scheme: g (host, nn x 3, copied) is the displacement field per unit
+ * load factor that the increment would produce in a homogeneous body, e.g.
+ * g = (X_x, 0, 0) for uniaxial extension along x with the end face at
+ * u_x = lambda L.  Every later boundary-condition update (fe_apply_bc, fe_step,
+ * fe_step_surrogate) moves the free DOFs by (lambda - lambda_prev) g before the
+ * one explicit update of the increment corrects them, so that a long bar loaded
+ * at its end is stretched along its whole length from the first increment on
+ * instead of in the elements next to the loaded face.  g = NULL removes the
+ * predictor.  RC_EINVAL for a non-finite g.  Synchronous. */
+int fe_set_predictor(fe_ctx *fe, const double *g);
 
 /* Element deformation gradients F_e = I + sum_a d_a (x) grad_X N_a (ne x 9) into
  * `where` memory.  Synchronous when where == RC_HOST. */

@@ -114,6 +114,7 @@ def lib():
         L.or_hex8_fint.argtypes = [D, D, C.c_double, D, D, C.c_double, D]
         L.or_fe_geometry.argtypes = [C.c_int, D, C.c_int, I, C.c_double, D, D, D]
         L.or_fe_apply_bc.argtypes = [C.c_int, I, D, C.c_double, D]
+        L.or_fe_apply_bc_pred.argtypes = [C.c_int, I, D, D, C.c_double, C.c_double, D]
         L.or_fe_F.argtypes = [C.c_int, I, D, D, D]
         L.or_fe_update.argtypes = [C.c_int, D, C.c_int, I, D, D, D, I, D, C.c_double, C.c_double, C.c_double,
                                    D, D, D]
@@ -328,8 +329,20 @@ class FEMesh:
         self.d = np.zeros((self.nn, 3))
         self.v = np.zeros((self.nn, 3))
 
+    g = None
+    lam_last = 0.0
+
+    def set_predictor(self, g):
+        """Affine predictor of the load increment (nn x 3, or None): see or_fe_apply_bc_pred."""
+        self.g = None if g is None else _f64(g, (-1, 3)).copy()
+
     def apply_bc(self, lam):
-        lib().or_fe_apply_bc(self.nn, _ip(self.bc_mask), _dp(self.bc_val), lam, _dp(self.d))
+        if self.g is None:
+            lib().or_fe_apply_bc(self.nn, _ip(self.bc_mask), _dp(self.bc_val), lam, _dp(self.d))
+        else:
+            lib().or_fe_apply_bc_pred(self.nn, _ip(self.bc_mask), _dp(self.bc_val), _dp(self.g), lam,
+                                      lam - self.lam_last, _dp(self.d))
+        self.lam_last = lam
 
     def F(self):
         F = np.zeros((self.ne, 3, 3))
@@ -347,6 +360,10 @@ class FEMesh:
 
 class FETetMesh:
     """Explicit 4-node tetrahedron FE driver state (FP64), the same step order as FEMesh."""
+
+    g = None
+    lam_last = 0.0
+    set_predictor = FEMesh.set_predictor
 
     def __init__(self, X, conn, bc_mask, bc_val, rho0, dt, damping):
         self.X = _f64(X, (-1, 3))
@@ -366,7 +383,12 @@ class FETetMesh:
         self.v = np.zeros((self.nn, 3))
 
     def apply_bc(self, lam):
-        lib().or_fe_apply_bc(self.nn, _ip(self.bc_mask), _dp(self.bc_val), lam, _dp(self.d))
+        if self.g is None:
+            lib().or_fe_apply_bc(self.nn, _ip(self.bc_mask), _dp(self.bc_val), lam, _dp(self.d))
+        else:
+            lib().or_fe_apply_bc_pred(self.nn, _ip(self.bc_mask), _dp(self.bc_val), _dp(self.g), lam,
+                                      lam - self.lam_last, _dp(self.d))
+        self.lam_last = lam
 
     def F(self):
         F = np.zeros((self.ne, 3, 3))

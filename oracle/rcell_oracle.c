@@ -770,6 +770,17 @@ void or_fe_apply_bc(int nn, const int *bc_mask, const double *bc_val, double lam
         if (bc_mask[k]) d[k] = lambda * bc_val[k];
 }
 
+/* The same with an affine predictor of the load increment: every free DOF moves
+ * by (lambda - lambda_prev) g before the explicit update, the prescribed ones
+ * take lambda bc_val (g NULL: no predictor). */
+void or_fe_apply_bc_pred(int nn, const int *bc_mask, const double *bc_val, const double *g, double lambda,
+                         double dlambda, double *d) {
+    for (int k = 0; k < 3 * nn; k++) {
+        if (bc_mask[k]) d[k] = lambda * bc_val[k];
+        else if (g) d[k] += dlambda * g[k];
+    }
+}
+
 /* per-element deformation gradients (ne x 9) */
 void or_fe_F(int ne, const int *conn, const double *gradN, const double *d, double *F) {
     for (int e = 0; e < ne; e++) {

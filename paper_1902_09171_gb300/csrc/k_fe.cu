@@ -61,10 +61,14 @@ __global__ void k_geometry(const double *__restrict__ X, const int *__restrict__
     for (int a = 0; a < NPE; a++) atomicAdd(&mass[conn[NPE * e + a]], rho0 * V / NPE);
 }
 
-__global__ void k_apply_bc(const int *__restrict__ mask, const double *__restrict__ val, double lambda, double *d,
-                           int n3) {
+// prescribed DOFs take lambda val; with an affine predictor g of the load
+// increment, every free DOF first moves by (lambda - lambda_prev) g
+__global__ void k_apply_bc(const int *__restrict__ mask, const double *__restrict__ val,
+                           const double *__restrict__ g, double lambda, double dlambda, double *d, int n3) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n3 && mask[q]) d[q] = lambda * val[q];
+    if (q >= n3) return;
+    if (mask[q]) d[q] = lambda * val[q];
+    else if (g) d[q] += dlambda * g[q];
 }
 
 template <int NPE>
@@ -245,10 +249,9 @@ void fe_launch_geometry(int npe, const double *X, const int *conn, int ne, doubl
     if (npe == 4) k_geometry<4><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
     else k_geometry<8><<<(ne + 127) / 128, 128, 0, s>>>(X, conn, ne, rho0, gradN, V0, mass, err);
 }
-void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
-                        cudaStream_t s) {
-    (void)v;
-    k_apply_bc<<<(n3 + 255) / 256, 256, 0, s>>>(mask, val, lambda, d, n3);
+void fe_launch_apply_bc(const int *mask, const double *val, const double *g, double lambda, double dlambda, double *d,
+                        int n3, cudaStream_t s) {
+    k_apply_bc<<<(n3 + 255) / 256, 256, 0, s>>>(mask, val, g, lambda, dlambda, d, n3);
 }
 void fe_launch_F(int npe, const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s) {
     if (npe == 4) k_F<4><<<(ne + 127) / 128, 128, 0, s>>>(conn, gradN, d, F, ne);

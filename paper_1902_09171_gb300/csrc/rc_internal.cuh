@@ -248,8 +248,8 @@ void rc_launch_keep_frozen(const KArrays &a, int cur_new, int n_tiles, cudaStrea
 // finite elements (k_fe.cu)
 void fe_launch_geometry(int npe, const double *X, const int *conn, int ne, double rho0, double *gradN, double *V0,
                         double *mass, int *err, cudaStream_t s);
-void fe_launch_apply_bc(const int *mask, const double *val, double lambda, double *d, double *v, int n3,
-                        cudaStream_t s);
+void fe_launch_apply_bc(const int *mask, const double *val, const double *g, double lambda, double dlambda, double *d,
+                        int n3, cudaStream_t s);
 void fe_launch_F(int npe, const int *conn, const double *gradN, const double *d, double *F, int ne, cudaStream_t s);
 void fe_launch_fint(int npe, const double *X, const int *conn, const double *gradN, const double *V0, const double *P,
                     const double *d, double hg, double *fint, int ne, cudaStream_t s);

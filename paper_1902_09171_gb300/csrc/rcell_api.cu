@@ -72,6 +72,9 @@ struct fe_ctx {
     double rho0 = 0, dt = 0, damping = 0, hg = 0;
     std::vector<void *> allocs;
     double *d_X = nullptr, *d_val = nullptr, *d_gradN = nullptr, *d_V0 = nullptr, *d_mass = nullptr;
+    double *d_g = nullptr;    // affine predictor of the load increment (nullptr: none)
+    double *d_g_buf = nullptr;
+    double lam_last = 0.0;    // load factor of the last boundary-condition update
     double *d_d = nullptr, *d_v = nullptr, *d_fint = nullptr, *d_F = nullptr, *d_P = nullptr;
     int *d_conn = nullptr, *d_mask = nullptr, *d_err = nullptr;
     cudaEvent_t ev = nullptr;
@@ -934,6 +937,11 @@ void rcell_destroy(rcell_ctx *c) {
 
 namespace {
 
+void apply_bc(fe_ctx *fe, double lambda, cudaStream_t s) {
+    fe_launch_apply_bc(fe->d_mask, fe->d_val, fe->d_g, lambda, lambda - fe->lam_last, fe->d_d, 3 * fe->nn, s);
+    fe->lam_last = lambda;
+}
+
 int fe_create_npe(int npe, const double *X, int nn, const int *conn, int ne, const int *bc_mask, const double *bc_val,
                   double rho0, double dt, double damping, double hg_coef, void *stream, fe_ctx **out) {
     const int *hex = conn;
@@ -997,8 +1005,24 @@ int fe_create_tet4(const double *X, int nn, const int *tet, int ne, const int *b
 
 int fe_apply_bc(fe_ctx *fe, double lambda) {
     if (!fe) return RC_EINVAL;
-    fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, fe->stream);
+    apply_bc(fe, lambda, fe->stream);
     CKF(fe, cudaGetLastError());
+    return RC_OK;
+}
+
+int fe_set_predictor(fe_ctx *fe, const double *g) {
+    if (!fe) return RC_EINVAL;
+    if (!g) {
+        fe->d_g = nullptr;  // the buffer stays allocated with the context
+        return RC_OK;
+    }
+    for (long k = 0; k < 3L * fe->nn; k++)
+        if (!std::isfinite(g[k])) return RC_EINVAL;
+    static_assert(sizeof(double) == 8, "");
+    if (!fe->d_g_buf) CKF(fe, dalloc(fe->allocs, &fe->d_g_buf, 3 * (size_t)fe->nn));
+    CKF(fe, cudaMemcpyAsync(fe->d_g_buf, g, sizeof(double) * 3 * fe->nn, cudaMemcpyHostToDevice, fe->stream));
+    CKF(fe, cudaStreamSynchronize(fe->stream));
+    fe->d_g = fe->d_g_buf;
     return RC_OK;
 }
 
@@ -1032,7 +1056,7 @@ int fe_step(fe_ctx *fe, rcell_ctx *rc, double lambda, int n_steps, int n_avg, do
     if (!fe || !rc) return RC_EINVAL;
     if (rc->n_cells != fe->ne) { fe->err = "one r-cell per element required"; return RC_EINVAL; }
     int e;
-    fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, fe->stream);
+    apply_bc(fe, lambda, fe->stream);
     fe_launch_F(fe->npe, fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, fe->ne, fe->stream);
     CKF(fe, cudaGetLastError());
     if (fe->stream != rc->stream) {
@@ -1082,7 +1106,7 @@ int fe_step_surrogate(fe_ctx *fe, rcell_ctx *rc, sur_ctx *sur, double lambda, in
     }
     int e;
     // 1. boundary conditions and element F
-    fe_launch_apply_bc(fe->d_mask, fe->d_val, lambda, fe->d_d, fe->d_v, 3 * fe->nn, st);
+    apply_bc(fe, lambda, st);
     fe_launch_F(fe->npe, fe->d_conn, fe->d_gradN, fe->d_d, fe->d_F, ne, st);
     // 2. surrogate for every point (keeps every recurrent state current)
     if ((e = sur_features(F_prev, fe->d_F, ne, fe->d_u, st)) != RC_OK) return e;

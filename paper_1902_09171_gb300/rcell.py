@@ -48,7 +48,7 @@ _lib = None
 EXPORTS = ["rcell_create", "rcell_set_deformation", "rcell_run", "rcell_stress", "rcell_eval", "rcell_get_energy",
            "rcell_get_atoms", "rcell_get_box", "rcell_get_neighbors", "rcell_get_series", "rcell_sync",
            "rcell_clear_status", "rcell_set_active", "rcell_set_limits", "rcell_set_staging", "rcell_set_tuning", "rcell_minimize", "rcell_stress_static", "rcell_get_rebuilds", "rcell_info", "rcell_profile_kernels", "rcell_fp32_peak", "rcell_checkpoint", "rcell_restore",
-           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_create_tet4", "fe_apply_bc", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
+           "rcell_stress_reduce_static", "rcell_last_error", "rcell_destroy", "fe_create", "fe_create_tet4", "fe_apply_bc", "fe_set_predictor", "fe_get_F", "fe_update", "fe_step", "fe_step_surrogate", "fe_get_P",
            "fe_get_state", "fe_destroy"]
 
 
@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "fe_create_tet4": ([vp, C.c_int, vp, C.c_int, vp, vp, C.c_double, C.c_double, C.c_double, vp,
                             C.POINTER(vp)], C.c_int),
         "fe_apply_bc": ([vp, C.c_double], C.c_int),
+        "fe_set_predictor": ([vp, vp], C.c_int),
         "fe_get_F": ([vp, vp, C.c_int], C.c_int),
         "fe_update": ([vp, vp, C.c_int], C.c_int),
         "fe_step": ([vp, vp, C.c_double, C.c_int, C.c_int, vp], C.c_int),
@@ -416,6 +417,15 @@ def fe_create_tet4(X, tet_conn, bc_mask, bc_val, rho0, dt, damping, stream=None)
 
 def fe_apply_bc(fe, lam: float):
     _check(load().fe_apply_bc(fe, lam), None, "fe_apply_bc")
+
+
+def fe_set_predictor(fe, g):
+    """Affine predictor of the load increment (nn x 3 host array), or None to remove it."""
+    if g is None:
+        _check(load().fe_set_predictor(fe, None), None, "fe_set_predictor")
+        return
+    arr = np.ascontiguousarray(g, dtype=np.float64)
+    _check(load().fe_set_predictor(fe, C.c_void_p(arr.ctypes.data)), None, "fe_set_predictor")
 
 
 def fe_get_F(fe, F):

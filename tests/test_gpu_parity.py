@@ -344,3 +344,33 @@ def test_checkpoint_restore_replays_identically():
         rcell.rcell_run(c.h, 40, 10)
         x2, v2, _ = rcell.rcell_get_atoms(c.h, 0, n)
     assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+
+
+def test_fe_with_affine_predictor_matches_oracle():
+    X, conn = inputs.hex_mesh(3, 2, 2, 3.0, 2.0, 2.0)
+    rng = np.random.default_rng(5)
+    inner = np.all((X > 1e-9) & (X < np.array([3.0, 2.0, 2.0]) - 1e-9), axis=1)
+    X[inner] += rng.uniform(-0.1, 0.1, (inner.sum(), 3))
+    mask, val = inputs.uniaxial_bc(X, 3.0)
+    g = np.zeros_like(X)
+    g[:, 0] = X[:, 0]
+    args = (X, conn, mask, val, 1.3, 0.05, 0.7, 0.4)
+    fe = rcell.fe_create(*args)
+    ref = oracle.FEMesh(*args)
+    rcell.fe_set_predictor(fe, g)
+    ref.set_predictor(g)
+    try:
+        for lam in (0.01, 0.02, 0.035):
+            rcell.fe_apply_bc(fe, lam)
+            ref.apply_bc(lam)
+            Fg = np.zeros((conn.shape[0], 3, 3))
+            rcell.fe_get_F(fe, Fg)
+            assert np.abs(Fg - ref.F()).max() < 1e-13
+            P = rng.standard_normal((conn.shape[0], 3, 3))
+            rcell.fe_update(fe, P)
+            ref.update(P)
+            d, v = rcell.fe_get_state(fe, X.shape[0])
+            assert np.abs(d - ref.d).max() < 1e-12 * max(1.0, np.abs(ref.d).max())
+            assert np.abs(v - ref.v).max() < 1e-12 * max(1.0, np.abs(ref.v).max())
+    finally:
+        rcell.fe_destroy(fe)

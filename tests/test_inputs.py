@@ -66,3 +66,31 @@ def test_feature_scales_floor_each_block_and_share_one_output_scale():
         assert np.allclose(u[a:b][big], std[a:b][big], rtol=1e-5)
     assert np.allclose(u[3], 0.1 * std[0:9].max(), rtol=1e-5) and np.allclose(u[12], 0.1 * std[9:15].max(), rtol=1e-5)
     assert np.all(y == y[0]) and abs(y[0] - np.sqrt((Y ** 2).mean())) <= 1e-5 * y[0]
+
+
+def test_bar_strain_paths_start_at_identity_and_stay_in_their_bounds():
+    n, T, ax, sh, lat, jit = 300, 25, 0.15, 0.12, 0.05, 0.005
+    F = inputs.bar_strain_paths(n, T, seed=13, max_axial=ax, max_shear=sh, max_lateral=lat, jitter=jit)
+    assert F.shape == (n, T + 1, 3, 3)
+    assert np.array_equal(F[:, 0], np.tile(np.eye(3), (n, 1, 1)))
+    assert np.all(np.linalg.det(F) > 0)
+    exx = F[:, :, 0, 0] - 1.0
+    assert exx.max() <= ax + jit + 1e-12 and exx.min() >= -0.2 * ax - jit - 1e-12
+    for (i, j) in ((0, 1), (0, 2), (1, 0), (2, 0)):
+        assert np.abs(F[:, :, i, j]).max() <= sh + jit + 1e-12
+        assert np.abs(F[:, -1, i, j]).max() > 0.5 * sh  # every shear is driven
+    assert np.abs(F[:, :, 1, 2]).max() <= jit + 1e-12  # the other shears only jitter
+    assert np.array_equal(F, inputs.bar_strain_paths(n, T, seed=13, max_axial=ax, max_shear=sh, max_lateral=lat,
+                                                      jitter=jit))
+
+
+def test_necking_mesh_has_the_imperfection_at_mid_length():
+    h = 28.66
+    X, conn = inputs.necking_mesh(32, 4, 4, h, 0.05)
+    X0, conn0 = inputs.hex_mesh(32, 4, 4, 32 * h, 4 * h, 4 * h)
+    assert np.array_equal(conn, conn0) and conn.shape == (512, 8)
+    moved = np.any(X != X0, axis=1)
+    assert np.allclose(X[moved, 0], 16 * h) and moved.sum() == 5 * 5 - 1  # the mid plane; its centre node stays
+    mid = np.abs(X[:, 0] - 16 * h) < 1e-9
+    area = (X[mid, 1].max() - X[mid, 1].min()) * (X[mid, 2].max() - X[mid, 2].min())
+    assert np.isclose(area, 0.95 * (4 * h) ** 2, rtol=1e-12)

@@ -95,3 +95,27 @@ def test_damped_explicit_update_reaches_static_bar_solution():
         fe.update(P)
     assert np.abs(fe.d[:, 0] - lam * X[:, 0]).max() < 1e-8
     assert np.abs(fe.d[:, 1:]).max() < 1e-8
+
+
+def test_affine_predictor_moves_free_nodes_affinely():
+    # with g = (X_x, 0, 0) and the end faces prescribed consistently, the predicted
+    # displacement of every node is lambda X_x: every element (a distorted mesh
+    # included) has F = I + lambda e_x (x) e_x exactly, increment after increment
+    X, conn = inputs.hex_mesh(4, 2, 2, 4.0, 2.0, 2.0)
+    rng = np.random.default_rng(3)
+    inner = np.all((X > 1e-9) & (X < np.array([4.0, 2.0, 2.0]) - 1e-9), axis=1)
+    X[inner] += rng.uniform(-0.15, 0.15, (inner.sum(), 3))
+    mask, val = inputs.uniaxial_bc(X, 4.0)
+    m = oracle.FEMesh(X, conn, mask, val, 1.0, 0.05, 0.5, 0.1)
+    g = np.zeros_like(X)
+    g[:, 0] = X[:, 0]
+    m.set_predictor(g)
+    for lam in (0.01, 0.025, 0.03):
+        m.apply_bc(lam)
+        F = m.F()
+        assert np.abs(F - np.diag([1.0 + lam, 1.0, 1.0])).max() < 1e-13
+        assert np.abs(m.d[:, 0] - lam * X[:, 0]).max() < 1e-13
+    # without the predictor only the prescribed DOFs move
+    m2 = oracle.FEMesh(X, conn, mask, val, 1.0, 0.05, 0.5, 0.1)
+    m2.apply_bc(0.01)
+    assert np.abs(m2.d[mask == 0]).max() == 0.0
