@@ -257,7 +257,10 @@ def bar_strain_paths(n_paths: int, n_inc: int, seed: int, max_axial: float = 0.1
     kind the elements of a bar in uniaxial tension go through: a monotone axial
     stretch to an amplitude in [-max_axial / 5, max_axial] along a ramp t^q
     (q in [0.5, 2]); lateral stretches -nu eps_x (nu in [0, 0.5]) plus their own
-    ramp in [-max_lateral, max_lateral / 4]; the four shears F_xy, F_xz, F_yx, F_zx
+    drift in [-max_lateral, max_lateral / 2] that saturates on a random time scale
+    (a few increments to the whole path: a thermal expansion that settles while the
+    Poisson contraction grows makes a lateral path that turns back); the four
+    shears F_xy, F_xz, F_yx, F_zx
     each ramped to an amplitude in [-max_shear, max_shear]; a random ramp of
     amplitude `jitter` in all nine components.  Returns (n_paths, n_inc + 1, 3, 3)."""
     rng = np.random.default_rng(seed)
@@ -268,7 +271,9 @@ def bar_strain_paths(n_paths: int, n_inc: int, seed: int, max_axial: float = 0.1
         nu = rng.uniform(0.0, 0.5)
         F[p, :, 0, 0] = 1.0 + ex
         for d in (1, 2):
-            F[p, :, d, d] = 1.0 - nu * ex + rng.uniform(-max_lateral, 0.25 * max_lateral) * t ** rng.uniform(0.5, 2.0)
+            drift = rng.uniform(-max_lateral, 0.5 * max_lateral)
+            tau = np.exp(rng.uniform(np.log(2.0 / n_inc), 0.0))
+            F[p, :, d, d] = 1.0 - nu * ex + drift * (1.0 - np.exp(-t / tau)) / (1.0 - np.exp(-1.0 / tau))
         for (i, j) in ((0, 1), (0, 2), (1, 0), (2, 0)):
             F[p, :, i, j] = rng.uniform(-max_shear, max_shear) * t ** rng.uniform(0.5, 2.0)
         F[p] += jitter * rng.uniform(-1, 1, (3, 3))[None] * t[:, None, None]
