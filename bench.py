@@ -190,7 +190,7 @@ NECK_BEADS, NECK_CHAIN, NECK_DENSITY = 20000, 50, 0.85
 NECK_INC, NECK_STRAIN, NECK_MD, NECK_AVG = 150, 0.6, 1000, 500
 NECK_IMPERFECTION = 0.05
 NECK_WORKLOAD = "necking_bar_kg_512x20000"
-NECK_SKINS, NECK_TPAS = (0.3, 0.4, 0.5, 0.6), (1, 2)
+NECK_SKINS, NECK_TPAS = (0.4, 0.5, 0.6, 0.7, 0.8), (0, 1, 2)  # lanes per atom 0: the lean walk
 
 # DRAM bytes (read + write) per bead of one k_force<KG> launch (non-sampling
 # variant), from an ncu capture of the necking-bar cells at a smaller batch; a
@@ -275,7 +275,7 @@ def run_necking_bar(args):
     # autotuned Verlet skin and lanes per atom, timed on 32 of this rank's cells
     make = lambda skin: rcell.params_kg(seed=11 + rank, skin=skin)  # noqa: E731
     if args.skin_kg > 0:
-        tuned, hit = {"skin": args.skin_kg, "tpa": args.tpa or 1, "table": []}, False
+        tuned, hit = {"skin": args.skin_kg, "tpa": args.tpa if args.tpa >= 0 else 1, "table": []}, False
     else:
         tuned, hit = autotune.tune(make, eq[:32], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=100)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
@@ -507,7 +507,7 @@ def run_ours(args):
     cells = make_cells(n_total, seed0=1000 + rank * n_total)
     prm = rcell.params_sc_cu(tau=0.1, kT=KT, dt=0.002, seed=12345 + rank, skin=args.skin)
     ctx = rcell.rcell_create(prm, cells, stream=stream)
-    if args.tpa:
+    if args.tpa >= 0:
         rcell.rcell_set_tuning(ctx, args.tpa, -1)
     rho0, dt_fe, damp_fe, hg_fe = fe_params()
     if args.element == "tet4":  # tetrahedra: shorter altitudes, half the step; no hourglass control
@@ -1156,7 +1156,7 @@ def main():
     ap.add_argument("--skin-kg", type=float, default=0.0, help="necking bar: fixed skin (0 = autotuned)")
     ap.add_argument("--element", default="hex8", choices=["hex8", "tet4"],
                     help="FE element of the copper bar: 8-node hexahedra (32 r-cells) or 4-node tetrahedra (192)")
-    ap.add_argument("--tpa", type=int, default=0)
+    ap.add_argument("--tpa", type=int, default=-1, help="lanes per atom (0: the lean walk; -1: default / autotuned)")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--distinct", type=int, default=16, help="necking bar: distinct seeded melts")

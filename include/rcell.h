@@ -189,8 +189,13 @@ int rcell_sync(rcell_ctx *ctx);
 int rcell_clear_status(rcell_ctx *ctx);
 
 /* Tuning knobs (chosen by the autotuner; any value < 0 keeps the current):
- *   threads_per_atom : 1, 2, 4 or 8 lanes cooperate on one atom's neighbours
- *   use_graphs       : 0/1, capture rcell_run into CUDA graphs */
+ *   threads_per_atom : 1, 2, 4 or 8 lanes cooperate on one atom's neighbours,
+ *                      walking the list software-pipelined (the next group's
+ *                      gathers in flight while a group is evaluated); 0 = one
+ *                      lane per atom with a plain walk compiled for more
+ *                      resident warps per SM (pays on large batches)
+ *   use_graphs       : 0/1, capture rcell_run into CUDA graphs
+ * All settings give the same results up to summation order. */
 int rcell_set_tuning(rcell_ctx *ctx, int threads_per_atom, int use_graphs);
 
 /* Failure-injection limits, with no counterpart in the paper (any value < 0

@@ -21,6 +21,9 @@
 
 namespace {
 
+// lanes that share one atom: TPA, or 1 for the lean walk (TPA == 0)
+__host__ __device__ constexpr int lanes_of(int tpa) { return tpa > 0 ? tpa : 1; }
+
 template <int TPA>
 __device__ __forceinline__ float sub_sum(float v) {
 #pragma unroll
@@ -125,6 +128,53 @@ __device__ __forceinline__ int4 clamp_group(int4 e, int left) {
     return e;
 }
 
+// Displacements and pair evaluations of one list group (entries e, records
+// c0..c3, `left` entries of the list from this group on).  Warp-uniform fast
+// paths for full groups: all four entries of the image slot 0 (the central
+// image: x_j - x_i, the bits rc_disp gives for it) in every converged lane, or
+// one image slot per lane's group (the runs of a stencil bin): one shift-table
+// read and one x_i - sp per group instead of one per entry, the same arithmetic
+// as rc_disp.
+template <class Fn>
+__device__ __forceinline__ void eval_group(const int4 &e, int left, const float4 &c0, const float4 &c1,
+                                           const float4 &c2, const float4 &c3, const float4 &xi, const ShiftTab &T,
+                                           Fn &&fn) {
+    const unsigned s0 = (unsigned)e.x >> RC_IDX_BITS;
+    const bool one_slot =
+        left >= 4 && (((unsigned)(e.x ^ e.y) | (unsigned)(e.x ^ e.z) | (unsigned)(e.x ^ e.w)) >> RC_IDX_BITS) == 0;
+    const unsigned am = __activemask();
+    float3 d0, d1, d2, d3;
+    if (__all_sync(am, one_slot && s0 == RC_SLOT_CENTRAL)) {
+        d0 = rc_disp_central(xi, c0);
+        d1 = rc_disp_central(xi, c1);
+        d2 = rc_disp_central(xi, c2);
+        d3 = rc_disp_central(xi, c3);
+    } else if (__all_sync(am, one_slot)) {
+        const float4 sa = T.a[s0], sb = T.b[s0];
+        const float4 xs = make_float4(xi.x - sb.x, xi.y - sb.y, xi.z - sb.z, sb.w);
+        d0 = rc_disp_pre(c0, sa, xs);
+        d1 = rc_disp_pre(c1, sa, xs);
+        d2 = rc_disp_pre(c2, sa, xs);
+        d3 = rc_disp_pre(c3, sa, xs);
+    } else {  // mixed image slots, or the list's last, partial group (whose missing
+              // entries repeat its first one: valid indices, results unused)
+        d0 = rc_disp(xi, c0, T, s0);
+        d1 = rc_disp(xi, c1, T, (unsigned)e.y >> RC_IDX_BITS);
+        d2 = rc_disp(xi, c2, T, (unsigned)e.z >> RC_IDX_BITS);
+        d3 = rc_disp(xi, c3, T, (unsigned)e.w >> RC_IDX_BITS);
+    }
+    if (left >= 4) {
+        fn(c0, d0);
+        fn(c1, d1);
+        fn(c2, d2);
+        fn(c3, d3);
+    } else {
+        fn(c0, d0);
+        if (left > 1) fn(c1, d1);
+        if (left > 2) fn(c2, d2);
+    }
+}
+
 // Walk one atom's Verlet list (this lane's share: groups sub, sub+TPA, ... of
 // four entries).  Each group is one 16-byte load.  The loop is software
 // pipelined: while the pairs of group g are evaluated, the four neighbour
@@ -132,10 +182,24 @@ __device__ __forceinline__ int4 clamp_group(int4 e, int left) {
 // the group after that are being loaded, so the gather latency overlaps the
 // pair arithmetic.  fn(xj, d) receives the neighbour's record and the exact
 // periodic displacement d = x_j(image) - x_i.
+// TPA == 0 is the lean walk: one lane per atom, one group at a time with no
+// pipelining -- fewer registers, so that more warps per SM hide the latency
+// instead (the kernels are compiled for 12 resident CTAs then), which pays
+// when the batch has enough tiles to fill them.
 template <int TPA, class Src, class Fn>
 __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub, const Src &src,
                                                   const float4 &xi, const ShiftTab &T, Fn &&fn) {
     const int ng = (nn + 3) >> 2;
+    if constexpr (TPA == 0) {
+        for (int g = 0; g < ng; g++) {
+            const int left = nn - 4 * g;
+            const int4 e = clamp_group(ld_list(nb4 + (size_t)g * RC_TILE), left);
+            const float4 c0 = src((unsigned)e.x & RC_IDX_MASK), c1 = src((unsigned)e.y & RC_IDX_MASK);
+            const float4 c2 = src((unsigned)e.z & RC_IDX_MASK), c3 = src((unsigned)e.w & RC_IDX_MASK);
+            eval_group(e, left, c0, c1, c2, c3, xi, T, fn);
+        }
+        return;
+    }
     int g = sub;
     if (g >= ng) return;
     int4 e = clamp_group(ld_list(nb4 + (size_t)g * RC_TILE), nn - 4 * g);
@@ -210,8 +274,13 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
 
 // Sutton-Chen density pass: rho_i = sum_j (a/r_ij)^m over r < rc; writes
 // xr_i = {x_i, rho_i^{-1/2}} for the force pass.
+// resident CTAs per SM the density pass is compiled for (a register cap of
+// 65536 / (128 x this) at one lane per atom): 12 for the lean walk, else 7 --
+// a 128 000-atom batch (1000 tiles) in one wave on 152 SMs
+constexpr int density_min_ctas(int tpa) { return tpa == 0 ? 12 : (7 / tpa > 0 ? 7 / tpa : 1); }
+
 template <int TPA, bool M6, bool STG>
-__global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, int cur) {
+__global__ void __launch_bounds__(RC_TILE *lanes_of(TPA), density_min_ctas(TPA)) k_density(KParams p, KArrays a, int cur) {
     extern __shared__ __align__(16) float4 s_cell[];
     rc_pdl_wait();
     rc_pdl_trigger();
@@ -223,7 +292,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA) k_density(KParams p, KArrays a, 
     __shared__ float s_H[8];
     rc_load_shifts(s_tab, s_H, a.Hf, c);
 
-    const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
+    const int at = threadIdx.x / lanes_of(TPA), sub = threadIdx.x % lanes_of(TPA);
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
     const float4 *__restrict__ X = cur ? a.x1 : a.x0;
@@ -281,13 +350,15 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
 #ifndef RC_FORCE_MIN_CTAS
 #define RC_FORCE_MIN_CTAS 7
 #endif
-constexpr int force_min_ctas(int tpa) { return RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1; }
+constexpr int force_min_ctas(int tpa) {
+    return tpa == 0 ? 12 : (RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1);
+}
 
 // SAMPLE: this launch records a stress sample (slot >= 0) or evaluates the
 // energy and virial (MODE_EVAL); without it the pair loop skips the virial and
 // energy terms, which only feed those records.
 template <int POT, int TPA, bool M6, bool STG, bool SAMPLE>
-__global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KParams p, KArrays a, int cur, int mode, int slot,
+__global__ void __launch_bounds__(RC_TILE *lanes_of(TPA), force_min_ctas(TPA)) k_force(KParams p, KArrays a, int cur, int mode, int slot,
                                                        int step_index) {
     extern __shared__ __align__(16) float4 s_cell[];
     rc_pdl_wait();
@@ -300,7 +371,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
     __shared__ float s_H[8];
     rc_load_shifts(s_tab, s_H, a.Hf, c);
 
-    const int at = threadIdx.x / TPA, sub = threadIdx.x % TPA;
+    const int at = threadIdx.x / lanes_of(TPA), sub = threadIdx.x % lanes_of(TPA);
     const int n = a.cell_n[c], off = a.cell_off[c];
     const int li = (t - a.cell_tile0[c]) * RC_TILE + at;
     const bool live = li < n;
@@ -454,7 +525,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
         if (own) a.f[g] = make_float4(fx, fy, fz, pe);
         float v[7] = {own ? pe : 0.f, own ? w0 : 0.f, own ? w1 : 0.f, own ? w2 : 0.f,
                       own ? w3 : 0.f, own ? w4 : 0.f, own ? w5 : 0.f};
-        block_reduce_add<7, RC_TILE * TPA>(v, a.eval_acc + 8 * c);
+        block_reduce_add<7, RC_TILE * lanes_of(TPA)>(v, a.eval_acc + 8 * c);
         return;
     }
 
@@ -512,7 +583,7 @@ __global__ void __launch_bounds__(RC_TILE *TPA, force_min_ctas(TPA)) k_force(KPa
         float v[13] = {kxx, kyy, kzz, kxy, kxz, kyz,
                        own ? w0 : 0.f, own ? w1 : 0.f, own ? w2 : 0.f, own ? w3 : 0.f, own ? w4 : 0.f, own ? w5 : 0.f,
                        own ? pe : 0.f};
-        block_reduce_add<13, RC_TILE * TPA>(v, a.series + ((size_t)c * a.series_cap + slot) * RC_SAMPLE_W);
+        block_reduce_add<13, RC_TILE * lanes_of(TPA)>(v, a.series + ((size_t)c * a.series_cap + slot) * RC_SAMPLE_W);
     }
 }
 
@@ -615,6 +686,7 @@ template <int POT, bool M6, bool STG, bool SAMPLE>
 void launch_force_tpa(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int mode, int slot,
                       int step_index, int smem, cudaStream_t s) {
     switch (tpa) {
+    case 0: rc_launch_pdl(k_force<POT, 0, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur, mode, slot, step_index); break;
     case 1: rc_launch_pdl(k_force<POT, 1, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur, mode, slot, step_index); break;
     case 2: rc_launch_pdl(k_force<POT, 2, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 2, smem, s, p, a, cur, mode, slot, step_index); break;
     case 4: rc_launch_pdl(k_force<POT, 4, M6, STG, SAMPLE>, pair_grid(p), RC_TILE * 4, smem, s, p, a, cur, mode, slot, step_index); break;
@@ -634,6 +706,7 @@ void launch_force_pot(const KParams &p, const KArrays &a, int cur, int n_tiles, 
 template <bool M6, bool STG>
 void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, int tpa, int smem, cudaStream_t s) {
     switch (tpa) {
+    case 0: rc_launch_pdl(k_density<0, M6, STG>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur); break;
     case 1: rc_launch_pdl(k_density<1, M6, STG>, pair_grid(p), RC_TILE * 1, smem, s, p, a, cur); break;
     case 2: rc_launch_pdl(k_density<2, M6, STG>, pair_grid(p), RC_TILE * 2, smem, s, p, a, cur); break;
     case 4: rc_launch_pdl(k_density<4, M6, STG>, pair_grid(p), RC_TILE * 4, smem, s, p, a, cur); break;
@@ -643,6 +716,7 @@ void launch_density_m(const KParams &p, const KArrays &a, int cur, int n_tiles, 
 
 template <int POT, bool M6, bool SAMPLE>
 void prepare_pot_s(int bytes) {
+    set_smem(k_force<POT, 0, M6, true, SAMPLE>, bytes);
     set_smem(k_force<POT, 1, M6, true, SAMPLE>, bytes);
     set_smem(k_force<POT, 2, M6, true, SAMPLE>, bytes);
     set_smem(k_force<POT, 4, M6, true, SAMPLE>, bytes);
@@ -657,6 +731,7 @@ void prepare_pot(int bytes) {
 
 template <bool M6>
 void prepare_density(int bytes) {
+    set_smem(k_density<0, M6, true>, bytes);
     set_smem(k_density<1, M6, true>, bytes);
     set_smem(k_density<2, M6, true>, bytes);
     set_smem(k_density<4, M6, true>, bytes);

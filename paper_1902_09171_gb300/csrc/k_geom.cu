@@ -74,7 +74,7 @@ __global__ void k_deform(const double *__restrict__ Fin, double *H, double *Rpre
             return;
         }
     int nb[3];
-    for (int k = 0; k < 3; k++) nb[k] = (int)floor(w[k] / rlist);
+    for (int k = 0; k < 3; k++) nb[k] = (int)floor(2.0 * w[k] / rlist);  // bins at least r_list / 2 wide
     while (nb[0] * nb[1] * nb[2] > bin_cap[c]) {
         int m = nb[0] >= nb[1] ? (nb[0] >= nb[2] ? 0 : 2) : (nb[1] >= nb[2] ? 1 : 2);
         nb[m]--;

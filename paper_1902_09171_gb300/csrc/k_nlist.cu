@@ -3,13 +3,15 @@
 //
 //  k_sort  : one CTA per r-cell.  Wraps positions into the current box through
 //            fractional coordinates, bins atoms on an n0 x n1 x n2 grid over the
-//            fractional cube (n_d = floor(w_d / r_list), w_d the perpendicular
-//            width), counting-sorts them by bin (stable, so the order is
-//            deterministic) and permutes every per-atom array.
-//  k_nlist : one thread per atom.  Scans the 27 neighbour bins with explicit
-//            periodic image shifts; with n_d >= 2 (guaranteed by w_d >= 2 r_list)
-//            each (bin, image) pair is visited once, so each (j, image) within
-//            r_list is stored exactly once.
+//            fractional cube (n_d = floor(2 w_d / r_list), w_d the perpendicular
+//            width: bins at least r_list / 2 wide), counting-sorts them by bin
+//            (stable, so the order is deterministic) and permutes every per-atom
+//            array.
+//  k_nlist : one thread per atom.  Scans the 5 x 5 x 5 bins around its own with
+//            explicit periodic image shifts (about 0.58 of the candidates of 27
+//            bins r_list wide); with n_d >= 2 (w_d >= 2 r_list gives n_d >= 4)
+//            the offsets -2..2 map to distinct (bin, image) pairs with images in
+//            -1..1, so each (j, image) within r_list is stored exactly once.
 #include "rc_internal.cuh"
 
 namespace {
@@ -207,13 +209,13 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
         // periodic images, so that the lanes of a warp walk long runs of
         // central entries, which skip the shift-table loads
         for (int sweep = 0; sweep < 2; sweep++)
-        for (int o0 = -1; o0 <= 1; o0++) {
+        for (int o0 = -2; o0 <= 2; o0++) {
             int u0 = b0 + o0, s0 = u0 < 0 ? -1 : (u0 >= nb0 ? 1 : 0);
             u0 -= s0 * nb0;
-            for (int o1 = -1; o1 <= 1; o1++) {
+            for (int o1 = -2; o1 <= 2; o1++) {
                 int u1 = b1 + o1, s1 = u1 < 0 ? -1 : (u1 >= nb1 ? 1 : 0);
                 u1 -= s1 * nb1;
-                for (int o2 = -1; o2 <= 1; o2++) {
+                for (int o2 = -2; o2 <= 2; o2++) {
                     int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
                     u2 -= s2 * nb2;
                     const int slot = rc_image_slot(s0, s1, s2);

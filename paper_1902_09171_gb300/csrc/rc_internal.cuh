@@ -10,6 +10,8 @@
 //     writes x(t+dt) of its own atoms).  Velocities: float4 {vx, vy, vz, 0}.
 //   * Inside a cell, atoms are kept sorted by neighbour bin (counting sort at
 //     every list rebuild); `tag` maps a slot back to the caller's atom index.
+//     Bins are at least r_list / 2 wide (in perpendicular width), so the
+//     candidates of an atom lie in the 5 x 5 x 5 bins around its own.
 //   * Verlet list: per tile, [max_nb/4][TILE] groups of four int32 entries
 //     j_global | (image << 27) (one 16-byte load per lane per group, coalesced
 //     across the tile); the image code 0..26 selects one of the 27 periodic
@@ -27,7 +29,7 @@
 #define RC_IDX_BITS 27
 #define RC_IDX_MASK ((1u << RC_IDX_BITS) - 1u)
 #define RC_MAX_BONDS 4
-#define RC_MAX_BINS_PER_CELL 4096
+#define RC_MAX_BINS_PER_CELL 8192
 #define RC_SAMPLE_W 14  // per-step sample record: K[6], W[6], pe, ke
 
 // per-step force-kernel modes

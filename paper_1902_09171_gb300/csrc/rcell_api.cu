@@ -255,7 +255,7 @@ int rcell_create(const rcell_params *params, int n_cells, const rcell_init *cell
         const double w[3] = {1 / std::sqrt(i00 * i00 + i01 * i01 + i02 * i02), 1 / std::sqrt(i11 * i11 + i12 * i12),
                              1 / std::fabs(i22)};
         long prod = 1;
-        for (int k = 0; k < 3; k++) prod *= std::max(1L, (long)std::floor(w[k] / c->rlist));
+        for (int k = 0; k < 3; k++) prod *= std::max(1L, (long)std::floor(2.0 * w[k] / c->rlist));
         bin_cap[i] = (int)std::min<long>(RC_MAX_BINS_PER_CELL, std::max<long>(64, 3 * prod));
         c->h_bin_off[i] = (int)bins;
         bins += bin_cap[i] + 1;
@@ -657,8 +657,9 @@ int rcell_set_limits(rcell_ctx *c, int max_neighbors, int wait_polls) {
 int rcell_set_tuning(rcell_ctx *c, int threads_per_atom, int use_graphs) {
     if (!c) return RC_EINVAL;
     if (threads_per_atom >= 0) {
-        if (threads_per_atom != 1 && threads_per_atom != 2 && threads_per_atom != 4 && threads_per_atom != 8)
-            return fail(c, RC_EINVAL, "threads_per_atom must be 1, 2, 4 or 8");
+        if (threads_per_atom != 0 && threads_per_atom != 1 && threads_per_atom != 2 && threads_per_atom != 4 &&
+            threads_per_atom != 8)
+            return fail(c, RC_EINVAL, "threads_per_atom must be 0 (lean walk), 1, 2, 4 or 8");
         if (threads_per_atom != c->tpa) free_graphs(c);
         c->tpa = threads_per_atom;
     }

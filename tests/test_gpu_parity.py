@@ -214,7 +214,7 @@ def test_kg_broken_bond_is_reported():
         assert rcell.STATUS[rcell.rcell_sync(c.h)] == "RC_EBOND"
 
 
-@pytest.mark.parametrize("tpa", [1, 2, 4, 8])
+@pytest.mark.parametrize("tpa", [0, 1, 2, 4, 8])
 def test_short_trajectory_matches_oracle(tpa):
     # same seed, same Philox counters: positions, velocities and per-step virial
     # stress of a 10-step Langevin run agree to FP32 accuracy
@@ -374,3 +374,28 @@ def test_fe_with_affine_predictor_matches_oracle():
             assert np.abs(v - ref.v).max() < 1e-12 * max(1.0, np.abs(ref.v).max())
     finally:
         rcell.fe_destroy(fe)
+
+
+@pytest.mark.parametrize("pot", ["lj", "sc", "kg"])
+def test_lean_walk_forces_match_oracle(pot):
+    # one lane per atom with the plain (not software-pipelined) list walk
+    if pot == "lj":
+        prm, cells = rcell.params_lj_cu(), [lj_cell(5, jit=0.15, seed=71)]
+    elif pot == "sc":
+        prm = rcell.params_sc_cu()
+        x, H = inputs.fcc(10, 10, 10, 3.615)
+        cells = [dict(H0=H, x0=inputs.to_f32(np.mod(inputs.jitter(x, 0.1, 72), H[0, 0])))]
+    else:
+        prm = rcell.params_kg()
+        x, H, bonds = inputs.kg_melt(20, 50, 0.85, seed=73, pushoff_iters=300)
+        cells = [dict(H0=H, x0=inputs.to_f32(x), bonds=bonds)]
+    with Ctx(prm, cells) as c:
+        rcell.rcell_set_tuning(c.h, 0, 1)
+        rcell.rcell_eval(c.h)
+        pe, W = rcell.rcell_get_energy(c.h)
+        x, _, f = rcell.rcell_get_atoms(c.h, 0, len(cells[0]["x0"]))
+        H, _, _ = rcell.rcell_get_box(c.h, 0)
+    fo, Wo, eo = oracle.forces(oracle_pot(prm), x, H, bonds=cells[0].get("bonds"))
+    assert force_err(f, fo) <= 1e-5
+    assert np.abs(W[0] - Wo).max() <= 1e-4 * np.abs(Wo).max()
+    assert abs(pe[0] - eo) <= 1e-5 * max(abs(eo), 1.0)
