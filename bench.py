@@ -685,7 +685,7 @@ def run_reference(args):
             tot_t += t
         value = tot_a / tot_t
         return {"impl": "reference",
-                "metric": "atom-steps/s batched r-cell MD (necking bar, %d Kremer-Grest r-cells x 20000 beads)" % ne,
+                "metric": "atom-steps/s batched r-cell MD (necking bar, %d Kremer-Grest r-cells x 20000 beads)" % int(np.prod(NECK_MESH)),
                 "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
