@@ -272,12 +272,13 @@ def run_necking_bar(args):
     ctx0, eq = pipeline.prepare_kg_batch(b - a, stream=stream, seed=7 + rank, soft_steps=args.soft_steps,
                                          eq_steps=args.eq_steps, cells=cells)
     rcell.rcell_destroy(ctx0)
-    # autotuned Verlet skin and lanes per atom, timed on 32 of this rank's cells
+    # autotuned Verlet skin and lanes per atom, timed (300 MD steps, a few list
+    # rebuilds per cell) on 32 of this rank's cells
     make = lambda skin: rcell.params_kg(seed=11 + rank, skin=skin)  # noqa: E731
     if args.skin_kg > 0:
         tuned, hit = {"skin": args.skin_kg, "tpa": args.tpa if args.tpa >= 0 else 1, "table": []}, False
     else:
-        tuned, hit = autotune.tune(make, eq[:32], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=100)
+        tuned, hit = autotune.tune(make, eq[:32], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=300)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     h = NECK_BEADS ** (1.0 / 3.0) / NECK_DENSITY ** (1.0 / 3.0)
@@ -753,7 +754,7 @@ def run_kg_bar(args):
     # autotuned Verlet skin and lanes per atom (timed on the bar's own cells)
     from paper_1902_09171_gb300 import autotune
     make = lambda skin: rcell.params_kg(skin=skin)  # noqa: E731
-    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=100)
+    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=300)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     rcell.rcell_run(ctx, 2000, 0)

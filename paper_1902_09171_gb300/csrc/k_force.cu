@@ -408,23 +408,24 @@ __global__ void __launch_bounds__(RC_TILE *lanes_of(TPA), force_min_ctas(TPA)) k
                     }
                     // dE/dr / r = eps / r^2 [ -n (a/r)^n + c m/2 (rho_i^-1/2 + rho_j^-1/2) (a/r)^m ]
                     const float gr = eps * ir2 * fmaf(cm2 * (xi.w + xj.w), arm, -sc_n * arn);
-                    fx = fmaf(gr, dx, fx);
-                    fy = fmaf(gr, dy, fy);
-                    fz = fmaf(gr, dz, fz);
-                    if (SAMPLE) {
-                        const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
-                        w0 = fmaf(hx, dx, w0);
-                        w1 = fmaf(hy, dy, w1);
-                        w2 = fmaf(-0.5f * gr * dz, dz, w2);
-                        w3 = fmaf(hx, dy, w3);
-                        w4 = fmaf(hx, dz, w4);
-                        w5 = fmaf(hy, dz, w5);
-                        pe = fmaf(0.5f * eps, arn, pe);
+                    const float gx = gr * dx, gy = gr * dy, gz = gr * dz;
+                    fx += gx;
+                    fy += gy;
+                    fz += gz;
+                    if (SAMPLE) {  // scaled once per atom after the walk: W by -1/2, pe by eps/2
+                        w0 = fmaf(gx, dx, w0);
+                        w1 = fmaf(gy, dy, w1);
+                        w2 = fmaf(gz, dz, w2);
+                        w3 = fmaf(gx, dy, w3);
+                        w4 = fmaf(gx, dz, w4);
+                        w5 = fmaf(gy, dz, w5);
+                        pe += arn;
                     }
                 }
             };
             if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
             else for_each_neighbor<TPA>(nb, nn, sub, GlobalSrc{XG}, xi, s_tab, body);
+            if (SAMPLE) pe *= 0.5f * eps;
         } else {
             const float s2 = p.sigma * p.sigma;
             const float c24 = 24.0f * p.eps, c2 = 2.0f * p.eps;
@@ -438,23 +439,32 @@ __global__ void __launch_bounds__(RC_TILE *lanes_of(TPA), force_min_ctas(TPA)) k
                     const float sr6 = sr2 * sr2 * sr2;
                     // dU/dr / r = -24 eps (2 (s/r)^12 - (s/r)^6) / r^2
                     const float gr = -c24 * ir2 * sr6 * (2.0f * sr6 - 1.0f);
-                    fx = fmaf(gr, dx, fx);
-                    fy = fmaf(gr, dy, fy);
-                    fz = fmaf(gr, dz, fz);
-                    if (SAMPLE) {
-                        const float hx = -0.5f * gr * dx, hy = -0.5f * gr * dy;
-                        w0 = fmaf(hx, dx, w0);
-                        w1 = fmaf(hy, dy, w1);
-                        w2 = fmaf(-0.5f * gr * dz, dz, w2);
-                        w3 = fmaf(hx, dy, w3);
-                        w4 = fmaf(hx, dz, w4);
-                        w5 = fmaf(hy, dz, w5);
-                        pe = fmaf(c2 * sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6)
+                    const float gx = gr * dx, gy = gr * dy, gz = gr * dz;
+                    fx += gx;
+                    fy += gy;
+                    fz += gz;
+                    if (SAMPLE) {  // scaled once per atom after the walk: W by -1/2, pe by 2 eps
+                        w0 = fmaf(gx, dx, w0);
+                        w1 = fmaf(gy, dy, w1);
+                        w2 = fmaf(gz, dz, w2);
+                        w3 = fmaf(gx, dy, w3);
+                        w4 = fmaf(gx, dz, w4);
+                        w5 = fmaf(gy, dz, w5);
+                        pe = fmaf(sr6, sr6 - 1.0f, pe);  // 1/2 * 4 eps (sr12 - sr6) / (2 eps)
                     }
                 }
             };
             if (STG) for_each_neighbor<TPA>(nb, nn, sub, SharedSrc{s_cell, off}, xi, s_tab, body);
             else for_each_neighbor<TPA>(nb, nn, sub, GlobalSrc{XG}, xi, s_tab, body);
+            if (SAMPLE) pe *= c2;
+        }
+        if (SAMPLE) {
+            w0 *= -0.5f;
+            w1 *= -0.5f;
+            w2 *= -0.5f;
+            w3 *= -0.5f;
+            w4 *= -0.5f;
+            w5 *= -0.5f;
         }
     }
     fx = sub_sum<TPA>(fx);

@@ -9,9 +9,10 @@
 //            array.
 //  k_nlist : one thread per atom.  Scans the 5 x 5 x 5 bins around its own with
 //            explicit periodic image shifts (about 0.58 of the candidates of 27
-//            bins r_list wide); with n_d >= 2 (w_d >= 2 r_list gives n_d >= 4)
-//            the offsets -2..2 map to distinct (bin, image) pairs with images in
-//            -1..1, so each (j, image) within r_list is stored exactly once.
+//            bins r_list wide), a row of five bins as one contiguous range; with
+//            n_d >= 2 (w_d >= 2 r_list gives n_d >= 4) the offsets -2..2 map to
+//            distinct (bin, image) pairs with images in -1..1, so each (j, image)
+//            within r_list is stored exactly once.
 #include "rc_internal.cuh"
 
 namespace {
@@ -207,7 +208,11 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
         if (p.pot == RC_POT_KG) pr = a.partner[g];
         // two sweeps of the stencil: central-image neighbours first, then the
         // periodic images, so that the lanes of a warp walk long runs of
-        // central entries, which skip the shift-table loads
+        // central entries, which skip the shift-table loads.  Bins are numbered
+        // with the third index fastest, so the five bins u2 = b2-2..b2+2 of a
+        // stencil row are one contiguous range of sorted atoms, split in up to
+        // three segments by their image along the third axis: the unwrapped
+        // bins (image 0), those wrapped below 0 (image -1) and above nb2 - 1 (+1).
         for (int sweep = 0; sweep < 2; sweep++)
         for (int o0 = -2; o0 <= 2; o0++) {
             int u0 = b0 + o0, s0 = u0 < 0 ? -1 : (u0 >= nb0 ? 1 : 0);
@@ -215,14 +220,28 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
             for (int o1 = -2; o1 <= 2; o1++) {
                 int u1 = b1 + o1, s1 = u1 < 0 ? -1 : (u1 >= nb1 ? 1 : 0);
                 u1 -= s1 * nb1;
-                for (int o2 = -2; o2 <= 2; o2++) {
-                    int u2 = b2 + o2, s2 = u2 < 0 ? -1 : (u2 >= nb2 ? 1 : 0);
-                    u2 -= s2 * nb2;
+                const int row = (u0 * nb1 + u1) * nb2;
+                for (int seg = 0; seg < 3; seg++) {
+                    int s2, lo, hi;
+                    if (seg == 0) {
+                        s2 = 0;
+                        lo = max(b2 - 2, 0);
+                        hi = min(b2 + 2, nb2 - 1);
+                    } else if (seg == 1) {
+                        if (b2 >= 2) continue;
+                        s2 = -1;
+                        lo = nb2 + b2 - 2;
+                        hi = nb2 - 1;
+                    } else {
+                        if (b2 + 2 < nb2) continue;
+                        s2 = 1;
+                        lo = 0;
+                        hi = b2 + 2 - nb2;
+                    }
                     const int slot = rc_image_slot(s0, s1, s2);
                     if ((slot == RC_SLOT_CENTRAL) != (sweep == 0)) continue;
-                    const int bb = (u0 * nb1 + u1) * nb2 + u2;
-                    const int j0 = bs[bb], j1 = bs[bb + 1];
-                    // one shift-table read per bin (the bin has one image slot); the
+                    const int j0 = bs[row + lo], j1 = bs[row + hi + 1];
+                    // one shift-table read per segment (it has one image slot); the
                     // candidates' records are loaded NBATCH at a time so that their
                     // loads overlap, then tested in order
                     const float4 sa = s_tab.a[slot], sb = s_tab.b[slot];
