@@ -190,7 +190,8 @@ NECK_BEADS, NECK_CHAIN, NECK_DENSITY = 20000, 50, 0.85
 NECK_INC, NECK_STRAIN, NECK_MD, NECK_AVG = 150, 0.6, 1000, 500
 NECK_IMPERFECTION = 0.05
 NECK_WORKLOAD = "necking_bar_kg_512x20000"
-NECK_SKINS, NECK_TPAS = (0.4, 0.5, 0.6, 0.7, 0.8), (0, 1, 2)  # lanes per atom 0: the lean walk
+NECK_SKINS, NECK_TPAS = (0.5, 0.6, 0.7, 0.8), (0, 1)  # lanes per atom 0: the lean walk
+NECK_TUNE_CELLS = 128  # a quarter of the bar: 20 000 tiles, enough waves to behave like the whole
 
 # DRAM bytes (read + write) per bead of one k_force<KG> launch (non-sampling
 # variant), from an ncu capture of the necking-bar cells at a smaller batch; a
@@ -272,13 +273,16 @@ def run_necking_bar(args):
     ctx0, eq = pipeline.prepare_kg_batch(b - a, stream=stream, seed=7 + rank, soft_steps=args.soft_steps,
                                          eq_steps=args.eq_steps, cells=cells)
     rcell.rcell_destroy(ctx0)
-    # autotuned Verlet skin and lanes per atom, timed (300 MD steps, a few list
-    # rebuilds per cell) on 32 of this rank's cells
+    # autotuned Verlet skin and lanes per atom, timed on 128 of this rank's cells
+    # (on 32 cells, under three waves of tiles, a longer list looked cheaper than
+    # it is on the whole bar) over 400 MD steps (a few list rebuilds per cell),
+    # the last 200 sampling the stress as the increments do
     make = lambda skin: rcell.params_kg(seed=11 + rank, skin=skin)  # noqa: E731
     if args.skin_kg > 0:
         tuned, hit = {"skin": args.skin_kg, "tpa": args.tpa if args.tpa >= 0 else 1, "table": []}, False
     else:
-        tuned, hit = autotune.tune(make, eq[:32], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=300)
+        tuned, hit = autotune.tune(make, eq[:NECK_TUNE_CELLS], stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=400,
+                                   n_avg=200)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     h = NECK_BEADS ** (1.0 / 3.0) / NECK_DENSITY ** (1.0 / 3.0)
@@ -406,6 +410,8 @@ def run_necking_bar(args):
                        "strain_per_increment": NECK_STRAIN / NECK_INC, "md_steps_per_increment": md, "n_avg": navg,
                        "skin": tuned["skin"], "threads_per_atom": int(tuned["tpa"]),
                        "autotune": "cache hit" if hit else ("fixed by --skin-kg" if args.skin_kg > 0 else "searched"),
+                       "autotune_ms_per_step": {f"skin {r['skin']} lanes {r['tpa']}": round(r["ms_per_step"], 4)
+                                                for r in tuned.get("table", [])},
                        "distinct_melts": args.distinct, "l2": "flushed (256 MB write) between steps",
                        "fe_predictor": "affine, g = (X_x, 0, 0)",
                        "parallelism": f"cells split over {world} GPUs, P all-gathered" if world > 1 else "single GPU"},
@@ -754,7 +760,7 @@ def run_kg_bar(args):
     # autotuned Verlet skin and lanes per atom (timed on the bar's own cells)
     from paper_1902_09171_gb300 import autotune
     make = lambda skin: rcell.params_kg(skin=skin)  # noqa: E731
-    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=300)
+    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=400, n_avg=200)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     rcell.rcell_run(ctx, 2000, 0)

@@ -2,7 +2,8 @@
 
 Tunables: the Verlet skin (list size versus rebuild frequency; fixed at
 context creation) and the number of lanes that share one atom's list
-(1, 2, 4 or 8; switchable on a live context).  Each candidate is timed on the
+(1, 2, 4 or 8 with the software-pipelined walk, or 0 for the lean walk;
+switchable on a live context).  Each candidate is timed on the
 caller's own batch -- the captured MD loop of `n_steps` steps after one warm-up
 run, with CUDA events on the batch's stream -- and the fastest is cached per
 (GPU name, potential, atom-count bucket) in a JSON file, so later runs on the
@@ -67,9 +68,11 @@ def search(make_params, cells, time_candidate, skins, tpas):
     return best, table
 
 
-def cuda_timer(stream, n_steps=100):
+def cuda_timer(stream, n_steps=100, n_avg=0):
     """Candidate timer for a CUDA batch: builds the context, runs one warm-up
-    (captures the graph), then times one run of n_steps steps."""
+    (captures the graph), then times one run of n_steps steps that records a
+    stress sample on the last n_avg of them (as a load increment does: sampling
+    steps evaluate the virial too, which makes long lists costlier)."""
     import torch
 
     def run(prm, cells, tpa):
@@ -79,10 +82,10 @@ def cuda_timer(stream, n_steps=100):
             return None  # e.g. skin too large for the box (r_list > w / 2)
         try:
             rcell.rcell_set_tuning(ctx, tpa, 1)
-            rcell.rcell_run(ctx, n_steps, 0)
+            rcell.rcell_run(ctx, n_steps, n_avg)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rcell.rcell_run(ctx, n_steps, 0)
+            rcell.rcell_run(ctx, n_steps, n_avg)
             e1.record(stream)
             torch.cuda.synchronize()
             if rcell.rcell_sync(ctx) != 0:
@@ -95,8 +98,9 @@ def cuda_timer(stream, n_steps=100):
 
 
 def tune(make_params, cells, stream, skins=(1.0, 1.5, 2.0), tpas=(1, 2, 4), n_steps=100, use_cache=True,
-         path: str = CACHE):
-    """Best (skin, tpa) for this GPU and workload, from the cache or by search."""
+         path: str = CACHE, n_avg=0):
+    """Best (skin, tpa) for this GPU and workload, from the cache or by search
+    (each candidate timed over n_steps MD steps, the last n_avg sampling)."""
     import torch
     gpu = torch.cuda.get_device_name()
     prm0 = make_params(skins[0])
@@ -106,7 +110,7 @@ def tune(make_params, cells, stream, skins=(1.0, 1.5, 2.0), tpas=(1, 2, 4), n_st
         hit = load_cache(path).get(k)
         if hit:
             return hit, True
-    best, table = search(make_params, cells, cuda_timer(stream, n_steps), skins, tpas)
+    best, table = search(make_params, cells, cuda_timer(stream, n_steps, n_avg), skins, tpas)
     value = dict(best, table=table)
     store(k, value, path)
     return value, False

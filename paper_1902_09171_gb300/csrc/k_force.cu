@@ -192,6 +192,9 @@ __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, 
     const int ng = (nn + 3) >> 2;
     if constexpr (TPA == 0) {
         for (int g = 0; g < ng; g++) {
+            // the list streams from DRAM: ask L2 for the group after next now, so
+            // that its load finds it there (no register holds it meanwhile)
+            if (g + 2 < ng) asm volatile("prefetch.global.L2 [%0];" ::"l"(nb4 + (size_t)(g + 2) * RC_TILE));
             const int left = nn - 4 * g;
             const int4 e = clamp_group(ld_list(nb4 + (size_t)g * RC_TILE), left);
             const float4 c0 = src((unsigned)e.x & RC_IDX_MASK), c1 = src((unsigned)e.y & RC_IDX_MASK);

@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     }
 }
 
-__global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur) {
+// compiled for 8 resident CTAs (64 registers): the rebuild is issue-bound, and
+// at the 96 registers it takes unbounded only 5 CTAs fit on an SM
+__global__ void __launch_bounds__(RC_TILE, 8) k_nlist(KParams p, KArrays a, int cur) {
     rc_pdl_wait();
     rc_pdl_trigger();
     const int t = blockIdx.x;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(RC_TILE) k_nlist(KParams p, KArrays a, int cur
                     // loads overlap, then tested in order
                     const float4 sa = s_tab.a[slot], sb = s_tab.b[slot];
                     const float4 xs = make_float4(xi.x - sb.x, xi.y - sb.y, xi.z - sb.z, sb.w);
-                    constexpr int NBATCH = 8;
+                    constexpr int NBATCH = 4;
                     for (int jb = j0; jb < j1; jb += NBATCH) {
                         float4 xj[NBATCH];
 #pragma unroll
