@@ -161,10 +161,11 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one k_force<SC> launch on this workload (128 000
-# atoms, skin 1.5 A), from an ncu capture of the current kernel (--set full,
-# the non-sampling variant): 121.91 MB read + 2.83 MB written.  Mostly the
-# Verlet list, re-read from DRAM every launch.
-K_FORCE_DRAM_BYTES = 124.75e6
+# atoms, skin 1.5 A), from an ncu capture of the current kernel (the variant
+# without a stress sample; the other one reads the same list): 121.91 MB read
+# + 2.72 MB written.  Mostly the Verlet list, re-read from DRAM every
+# launch.
+K_FORCE_DRAM_BYTES = 124.63e6
 
 
 def fp32_unit_peak_tflops():
@@ -193,12 +194,12 @@ NECK_WORKLOAD = "necking_bar_kg_512x20000"
 NECK_SKINS, NECK_TPAS = (0.4, 0.5, 0.6, 0.7), (0, 1)  # lanes per atom 0: the lean walk
 NECK_TUNE_CELLS = 128  # a quarter of the bar: 20 000 tiles, enough waves to behave like the whole
 
-# DRAM bytes (read + write) per bead of one k_force<KG> launch (non-sampling
-# variant), from an ncu capture of the necking-bar cells at a smaller batch; a
-# launch's traffic grows in proportion to its beads (lists, positions and
-# velocities are per bead).  None until a capture of the current kernel exists.
-K_FORCE_KG_DRAM_BYTES_PER_ATOM = None
-K_FORCE_KG_SKIN = None  # the Verlet skin of that capture (the list length depends on it)
+# DRAM bytes (read + write) per bead of one k_force<KG> launch (the lean walk,
+# non-sampling variant), by Verlet skin, from ncu captures of 16 necking-bar
+# cells (320 000 beads): skin 0.4: 146.77 + 6.06 MB, skin 0.5: 160.23 + 6.09 MB.
+# A launch's traffic grows in proportion to its beads (lists, positions and
+# velocities are per bead); the list length depends on the skin.
+K_FORCE_KG_DRAM_BYTES_PER_ATOM = {0.4: 152.83e6 / 320000, 0.5: 166.32e6 / 320000}
 
 
 def kg_algorithmic_flops_per_atom_step(rho, bonds_per_atom):
@@ -385,8 +386,8 @@ def run_necking_bar(args):
     t_ns, t_s = prof["force"], prof.get("force_sample", prof["force"])
     n_local = NECK_BEADS * (b - a)
     achieved = (n_ns * f_ns + n_s * f_s) * n_local / ((n_ns * t_ns + n_s * t_s) / 1e3) / 1e12
-    traffic = (K_FORCE_KG_DRAM_BYTES_PER_ATOM * n_local
-               if (K_FORCE_KG_DRAM_BYTES_PER_ATOM is not None and tuned["skin"] == K_FORCE_KG_SKIN) else None)
+    per_bead = K_FORCE_KG_DRAM_BYTES_PER_ATOM.get(float(tuned["skin"])) if int(tuned["tpa"]) == 0 else None
+    traffic = round(per_bead * n_local) if per_bead is not None else None
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
                 "kernel": "k_force<KG> (LJ + FENE/WCA forces, Verlet/Langevin, virial on sampling steps)",
