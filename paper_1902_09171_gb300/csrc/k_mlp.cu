@@ -558,91 +558,170 @@ __device__ __forceinline__ void ws_bulk(unsigned char *sW, const unsigned char *
                  : "memory");
 }
 
-// input rows of step t: columns 0..14 (u_t * u_inv) and the pad column, by `nthr` threads
-__device__ __forceinline__ void ws_build_u(const FusedArgs &a, long tzo, unsigned char *sZ, int m0, int t, int tid,
-                                           int nthr) {
-    const bool tape = a.tZ != nullptr;
-    for (int idx = tid; idx < FT_M * 16; idx += nthr) {
-        const int r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1, bb = m0 + r;
-        const float v = (j < NIN && bb < a.B) ? a.U[((size_t)bb * a.T + t) * NIN + j] * a.u_inv[j] : 0.0f;
-        const unsigned short hv = bf16_bits(v);
-        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = hv;
-        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ + tzo)[((size_t)t * a.B + bb) * K0 + col] = hv;
+// Input rows of step t: columns 0..14 (u_t * u_inv) and the pad column, by the
+// WS_EPI_WARPS * 32 epilogue threads, WS_U_PER thread each.  ws_load_u reads
+// the features into registers (issued before the head layer's accumulator is
+// ready, so that the global-memory latency runs under its MMAs); ws_store_u
+// writes them into the operand.
+constexpr int WS_U_PER = FT_M * 16 / (WS_EPI_WARPS * 32);
+static_assert(WS_U_PER * WS_EPI_WARPS * 32 == FT_M * 16, "input columns per epilogue thread");
+__device__ __forceinline__ void ws_load_u(const FusedArgs &a, int m0, int t, int tid, float (&v)[WS_U_PER]) {
+#pragma unroll
+    for (int k = 0; k < WS_U_PER; k++) {
+        const int idx = tid + k * WS_EPI_WARPS * 32, r = idx >> 4, j = idx & 15, bb = m0 + r;
+        v[k] = (j < NIN && bb < a.B) ? a.U[((size_t)bb * a.T + t) * NIN + j] * a.u_inv[j] : 0.0f;
+    }
+}
+__device__ __forceinline__ void ws_store_u(unsigned char *sZ, int tid, const float (&v)[WS_U_PER]) {
+#pragma unroll
+    for (int k = 0; k < WS_U_PER; k++) {
+        const int idx = tid + k * WS_EPI_WARPS * 32, r = idx >> 4, j = idx & 15, col = j < NIN ? j : K0 - 1;
+        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, col, FT_M)) = bf16_bits(v[k]);
     }
 }
 
 // the state columns of step 0 (given h, or zero)
-__device__ __forceinline__ void ws_build_h0(const FusedArgs &a, long tzo, unsigned char *sZ, const float *h, int m0,
-                                            int tid, int nthr) {
-    const bool tape = a.tZ != nullptr;
+__device__ __forceinline__ void ws_build_h0(const FusedArgs &a, unsigned char *sZ, const float *h, int m0, int tid,
+                                            int nthr) {
     for (int idx = tid; idx < FT_M * NH; idx += nthr) {
         const int r = idx / NH, j = idx - r * NH, bb = m0 + r;
         const float v = (h && bb < a.B) ? h[(size_t)bb * NH + j] : 0.0f;
-        const unsigned short hv = bf16_bits(v);
-        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = hv;
-        if (tape && bb < a.B) reinterpret_cast<unsigned short *>(a.tZ + tzo)[(size_t)bb * K0 + NIN + j] = hv;
+        *reinterpret_cast<unsigned short *>(sZ + cm_off(r, NIN + j, FT_M)) = bf16_bits(v);
     }
 }
 
-// epilogue of layer l at step t for one warp: its 32 accumulator rows (lane
-// quarter), its column part, 16 columns at a time
-__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tzo, long tyo, int l, int t, int quarter,
+// The 144-column operand rows of a step (the forward's input rows z_t =
+// [u_t, h_{t-1}, 0], the backward's dO_{t-1}), complete in shared memory once
+// every epilogue warp has arrived on the hand-over barrier, copied to the tape
+// in pieces of 8 columns (16 bytes; 18 pieces a row; row bb of the batch at
+// dst + bb * K0).  Each warp copies the pieces that its own next epilogue
+// overwrites (the rows of its lane quarter, the 8 pieces of its column part),
+// so that no other warp can overwrite a piece before it has been copied.
+__device__ __forceinline__ void ws_tape_rows(__nv_bfloat16 *dst, int B, const unsigned char *sZA, int m0, int quarter,
+                                             int part, int lane) {
+    constexpr int KG = K0 / 8;
+    static_assert(KG * 8 == K0, "whole pieces per row");
+    const int kg0 = part * 8, npc = min(KG - kg0, 8);
+    if (npc <= 0) return;
+    for (int i = lane; i < 32 * npc; i += 32) {
+        const int r = quarter * 32 + i / npc, kg = kg0 + i % npc, bb = m0 + r;
+        if (bb < B)
+            *reinterpret_cast<uint4 *>(dst + (size_t)bb * K0 + kg * 8) =
+                *reinterpret_cast<const uint4 *>(sZA + cm_off(r, kg * 8, FT_M));
+    }
+}
+
+// 16 accumulator columns of the warp's lane quarter (32 rows, one per lane)
+// from tensor memory into r.  The load is asynchronous: r may be read only
+// after tmem_wait16(r).
+__device__ __forceinline__ void tmem_ld16(unsigned (&r)[16], unsigned taddr) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Waits for every tensor-memory load this thread has issued.  The registers of
+// r pass through the statement, so no use of the loaded values can be
+// scheduled above the wait.
+__device__ __forceinline__ void tmem_wait16(unsigned (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// hidden layer l < 3, columns n0 .. n0 + 15 of row `row`: bias, GELU, the BF16
+// operand of the next layer in shared memory, and the tape (y, a) if recorded
+__device__ __forceinline__ void ws_act16(const FusedArgs &a, long tyo, int l, int t, int row, int b, int n0,
+                                         const unsigned (&r)[16], unsigned char *sZA, const float *s_bias) {
+    const float4 *bias = reinterpret_cast<const float4 *>(s_bias + l * WID + n0);
+    unsigned yp[8], ap[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+        const float4 bv = bias[j >> 2];
+        const float v0 = __uint_as_float(r[j]) + bv.x, v1 = __uint_as_float(r[j + 1]) + bv.y;
+        const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
+        yp[j >> 1] = bf16x2_bits(v0, v1);
+        yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
+        ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
+        ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
+    }
+    const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
+    *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
+    *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = a1;
+    if (a.tZ != nullptr && b < a.B) {
+        const size_t o = tyo + ((size_t)t * a.B + b) * WID + n0;
+        st_v8(a.tY[l] + o, make_uint4(yp[0], yp[1], yp[2], yp[3]), make_uint4(yp[4], yp[5], yp[6], yp[7]));
+        st_v8(a.tA[l] + o, a0, a1);
+    }
+}
+
+// head layer, columns n0 .. n0 + 15 of row `row`: the stress outputs and the
+// next state (tanh) into the state columns of the next step's input rows
+__device__ __forceinline__ void ws_head16(const FusedArgs &a, int t, int row, int b, int n0, const unsigned (&r)[16],
+                                          unsigned char *sZA, const float *s_bias, float *S, float *h) {
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const int n = n0 + j;
+        const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
+        if (n < NOUT) {
+            if (b < a.B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
+        } else if (n < NOUT + NH) {
+            const float hv = tanhf(o);
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = bf16_bits(hv);
+            if (h && b < a.B && t + 1 == a.T) h[(size_t)b * NH + n - NOUT] = hv;
+        }
+    }
+}
+
+// Epilogue of layer l at step t for one warp: its 32 accumulator rows (lane
+// quarter) and its column part, 16 columns at a time, with the load of the next
+// 16 columns from tensor memory in flight while the current ones are processed
+// (two register sets, straight-line code: no register that a load is still
+// filling is copied or read before its wait).
+static_assert(WID / 16 == 4 * FT_PARTS, "a hidden layer's part is four 16-column chunks");
+static_assert(N4 / 16 == 9 && FT_PARTS == 4, "the head's parts are 2, 2, 2 and 3 chunks");
+static_assert(N4 == K0, "the head's output rows and the input rows have the same width");
+__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tyo, int l, int t, int quarter,
                                             int part, int lane, unsigned tmem, unsigned char *sZA,
                                             const float *s_bias, float *S, float *h, int m0) {
-    const bool tape = a.tZ != nullptr;
-    const int B = a.B, T = a.T, row = quarter * 32 + lane, b = m0 + row;
-    const int Nl = l == 3 ? N4 : WID;
-    const int nch = Nl >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
-    for (int ch = ch0; ch < ch1; ch++) {
-        const int n0 = ch * 16;
-        unsigned r[16];
-        const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];\n"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (l < 3) {
-            const float4 *bias = reinterpret_cast<const float4 *>(s_bias + l * WID + n0);
-            unsigned yp[8], ap[8];
-#pragma unroll
-            for (int j = 0; j < 16; j += 4) {
-                const float4 bv = bias[j >> 2];
-                const float v0 = __uint_as_float(r[j]) + bv.x, v1 = __uint_as_float(r[j + 1]) + bv.y;
-                const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
-                yp[j >> 1] = bf16x2_bits(v0, v1);
-                yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
-                ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
-                ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
-            }
-            const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
-            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
-            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = a1;
-            if (tape && b < B) {
-                st_v8(a.tY[l] + tyo + ((size_t)t * B + b) * WID + n0, make_uint4(yp[0], yp[1], yp[2], yp[3]),
-                      make_uint4(yp[4], yp[5], yp[6], yp[7]));
-                st_v8(a.tA[l] + tyo + ((size_t)t * B + b) * WID + n0, a0, a1);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int n = n0 + j;
-                const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
-                if (n < NOUT) {
-                    if (b < B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
-                } else if (n < NOUT + NH) {
-                    const float hv = tanhf(o);
-                    const unsigned short hb = bf16_bits(hv);
-                    *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = hb;
-                    if (tape && b < B && t + 1 < T)
-                        reinterpret_cast<unsigned short *>(a.tZ + tzo)[((size_t)(t + 1) * B + b) * K0 + NIN + n - NOUT] = hb;
-                    if (h && b < B && t + 1 == T) h[(size_t)b * NH + n - NOUT] = hv;
-                }
-            }
-        }
+    const int row = quarter * 32 + lane, b = m0 + row;
+    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
+    unsigned ra[16], rb[16];
+    if (l < 3) {
+        const int c = part * 64;
+        tmem_ld16(ra, tq + c);
+        tmem_wait16(ra);
+        tmem_ld16(rb, tq + c + 16);
+        ws_act16(a, tyo, l, t, row, b, c, ra, sZA, s_bias);
+        tmem_wait16(rb);
+        tmem_ld16(ra, tq + c + 32);
+        ws_act16(a, tyo, l, t, row, b, c + 16, rb, sZA, s_bias);
+        tmem_wait16(ra);
+        tmem_ld16(rb, tq + c + 48);
+        ws_act16(a, tyo, l, t, row, b, c + 32, ra, sZA, s_bias);
+        tmem_wait16(rb);
+        ws_act16(a, tyo, l, t, row, b, c + 48, rb, sZA, s_bias);
+        return;
+    }
+    const int c = part * 32;  // chunks 2 part, 2 part + 1 (and 8 for the last part)
+    tmem_ld16(ra, tq + c);
+    tmem_wait16(ra);
+    tmem_ld16(rb, tq + c + 16);
+    ws_head16(a, t, row, b, c, ra, sZA, s_bias, S, h);
+    tmem_wait16(rb);
+    if (part == FT_PARTS - 1) {
+        tmem_ld16(ra, tq + c + 32);
+        ws_head16(a, t, row, b, c + 16, rb, sZA, s_bias, S, h);
+        tmem_wait16(ra);
+        ws_head16(a, t, row, b, c + 32, ra, sZA, s_bias, S, h);
+    } else {
+        ws_head16(a, t, row, b, c + 16, rb, sZA, s_bias, S, h);
     }
 }
 
@@ -756,22 +835,38 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     } else {
         // ---- epilogue warps ----
         const int etid = tid, nthr = WS_EPI_WARPS * 32, quarter = warp & 3, part = warp >> 2;
-        ws_build_u(a, tzo, sZA, m0, 0, etid, nthr);
-        ws_build_h0(a, tzo, sZA, h, m0, etid, nthr);
+        const bool tape = a.tZ != nullptr;
+        float uv[WS_U_PER];
+        ws_load_u(a, m0, 0, etid, uv);
+        ws_store_u(sZA, etid, uv);
+        ws_build_h0(a, sZA, h, m0, etid, nthr);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+        // z rows to the tape: after the initial build and after every head epilogue
+        // the hand-over barrier completes a phase of parity 0 (phase 4 t + 4)
+        if (tape) {
+            ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+            if (ok) ws_tape_rows(a.tZ + tzo, a.B, sZA, m0, quarter, part, lane);
+            __syncwarp();
+        }
         for (int t = 0; t < T && ok; t++)
             for (int l = 0; l < 4 && ok; l++) {
+                if (l == 3 && t + 1 < T) ws_load_u(a, m0, t + 1, etid, uv);
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((t * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                ws_epilogue(a, tzo, tyo, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
-                if (l == 3 && t + 1 < T) ws_build_u(a, tzo, sZA, m0, t + 1, etid, nthr);
+                ws_epilogue(a, tyo, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
+                if (l == 3 && t + 1 < T) ws_store_u(sZA, etid, uv);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+                if (tape && l == 3 && t + 1 < T) {
+                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+                    if (ok) ws_tape_rows(a.tZ + tzo + (size_t)(t + 1) * a.B * K0, a.B, sZA, m0, quarter, part, lane);
+                    __syncwarp();
+                }
             }
         if (!ok && lane == 0) atomicExch(a.err, RC_ETIMEOUT);
     }
@@ -1046,84 +1141,134 @@ __device__ __forceinline__ float wb_stress_grad(const BwdArgs &a, const float *S
     return a.gscale * (S[i] - a.Y[i] * a.s_inv[n]);
 }
 
+// Columns c0 .. c0 + 31 of the tape row Y_{3-l} of step t (row b) into
+// registers (zero past the batch).  The first half of a part is loaded before
+// the layer's accumulator is ready, so that the global-memory latency runs
+// under the layer's MMAs; the second half while the first is processed.
+__device__ __forceinline__ void wb_load_y(const BwdArgs &a, long yo, int l, int t, int c0, int b, uint4 (&y)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) y[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (l < 3 && b < a.B) {
+        const __nv_bfloat16 *Yg = a.Yt[2 - l] + yo + ((size_t)t * a.B + b) * WID + c0;
+        ld_v8(Yg, y[0], y[1]);
+        ld_v8(Yg + 16, y[2], y[3]);
+    }
+}
+
+// What the warp's epilogue of product l at step t reads from the tape, loaded
+// before the accumulator is ready: for a hidden layer the first 32 of its 64
+// columns of Y_{3-l}, for dZ columns part * 32 .. part * 32 + 31 of the Z row.
+__device__ __forceinline__ void wb_prefetch(const BwdArgs &a, long yo, long zo, int l, int t, int part, int b,
+                                            uint4 (&y)[4]) {
+    if (l < 3) {
+        wb_load_y(a, yo, l, t, part * 64, b, y);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) y[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (t > 0 && b < a.B) {
+        const __nv_bfloat16 *Zg = a.Z + zo + ((size_t)t * a.B + b) * K0 + part * 32;
+        ld_v8(Zg, y[0], y[1]);
+        ld_v8(Zg + 16, y[2], y[3]);
+    }
+}
+
+// dY = acc * gelu'(Y) for columns n0 .. n0 + 15 of row `row`: the next
+// operand in shared memory and the dY rows in global memory
+__device__ __forceinline__ void wb_dy16(const BwdArgs &a, long yo, int l, int t, int row, int b, int n0,
+                                        const unsigned (&r)[16], const uint4 &y0, const uint4 &y1,
+                                        unsigned char *sZA) {
+    const unsigned yw[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+    unsigned dp[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const __nv_bfloat162 yy = *reinterpret_cast<const __nv_bfloat162 *>(&yw[j]);
+        const float g0 = __uint_as_float(r[2 * j]) * gelu_grad_as(__low2float(yy));
+        const float g1 = __uint_as_float(r[2 * j + 1]) * gelu_grad_as(__high2float(yy));
+        dp[j] = bf16x2_bits(g0, g1);
+    }
+    const uint4 d0 = make_uint4(dp[0], dp[1], dp[2], dp[3]), d1 = make_uint4(dp[4], dp[5], dp[6], dp[7]);
+    *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = d0;
+    *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = d1;
+    if (b < a.B) st_v8(a.dY[2 - l] + yo + ((size_t)t * a.B + b) * WID + n0, d0, d1);
+}
+
+// dO state columns from dZ for accumulator columns n0 .. n0 + 15 of row
+// `row`, into the next operand: dZ(h) * (1 - h^2) (the tanh of the state), h
+// from the Z tape words z
+__device__ __forceinline__ void wb_dz16(int row, int n0, const unsigned (&r)[16], const uint4 &z0, const uint4 &z1,
+                                        unsigned char *sZA) {
+    const unsigned zw[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const int n = n0 + j;
+        if (n >= NIN && n < NIN + NH) {
+            const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(&zw[j >> 1]);
+            const float h = (j & 1) ? __high2float(hh) : __low2float(hh);
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NOUT + n - NIN, FT_M)) =
+                bf16_bits(__uint_as_float(r[j]) * (1.0f - h * h));
+        }
+    }
+}
+
+// Epilogue of backward product l at step t for one warp (lane quarter, column
+// part); y holds the first 32 columns of the part's tape row (wb_load_y).
+// Hidden layers pipeline the tensor-memory loads as the forward epilogue does.
 __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, long oo, int l, int t, int quarter,
                                             int part, int lane, unsigned tmem, unsigned char *sZA, const float *S,
-                                            int m0) {
+                                            int m0, const uint4 (&y)[4]) {
     const int B = a.B, row = quarter * 32 + lane, b = m0 + row;
     const bool live = b < B;
     if (l < 3) {  // dY_{3-l} = acc * gelu'(Y_{3-l})
-        const __nv_bfloat16 *Yg = a.Yt[2 - l] + yo + ((size_t)t * B + b) * WID;
-        __nv_bfloat16 *dY = a.dY[2 - l] + yo + ((size_t)t * B + b) * WID;
-        const int nch = WID >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
-        for (int ch = ch0; ch < ch1; ch++) {
-            const int n0 = ch * 16;
-            unsigned r[16];
-            const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];\n"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(taddr)
-                : "memory");
-            uint4 y0 = make_uint4(0u, 0u, 0u, 0u), y1 = y0;
-            if (live) ld_v8(Yg + n0, y0, y1);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const unsigned yw[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-            unsigned dp[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const __nv_bfloat162 yy = *reinterpret_cast<const __nv_bfloat162 *>(&yw[j]);
-                const float g0 = __uint_as_float(r[2 * j]) * gelu_grad_as(__low2float(yy));
-                const float g1 = __uint_as_float(r[2 * j + 1]) * gelu_grad_as(__high2float(yy));
-                dp[j] = bf16x2_bits(g0, g1);
-            }
-            const uint4 d0 = make_uint4(dp[0], dp[1], dp[2], dp[3]), d1 = make_uint4(dp[4], dp[5], dp[6], dp[7]);
-            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = d0;
-            *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0 + 8, FT_M)) = d1;
-            if (live) st_v8(dY + n0, d0, d1);
-        }
+        const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
+        const int c = part * 64;
+        unsigned ra[16], rb[16];
+        uint4 y2[4];
+        tmem_ld16(ra, tq + c);
+        wb_load_y(a, yo, l, t, c + 32, b, y2);
+        tmem_wait16(ra);
+        tmem_ld16(rb, tq + c + 16);
+        wb_dy16(a, yo, l, t, row, b, c, ra, y[0], y[1], sZA);
+        tmem_wait16(rb);
+        tmem_ld16(ra, tq + c + 32);
+        wb_dy16(a, yo, l, t, row, b, c + 16, rb, y[2], y[3], sZA);
+        tmem_wait16(ra);
+        tmem_ld16(rb, tq + c + 48);
+        wb_dy16(a, yo, l, t, row, b, c + 32, ra, y2[0], y2[1], sZA);
+        tmem_wait16(rb);
+        wb_dy16(a, yo, l, t, row, b, c + 48, rb, y2[2], y2[3], sZA);
         return;
     }
-    // dZ_t -> dO_{t-1}; nothing to hand on after step 0
+    // dZ_t -> dO_{t-1}; nothing to hand on after step 0.  y holds columns
+    // part * 32 .. part * 32 + 31 of the Z tape row [u_t, h_{t-1}, 0]
+    // (wb_prefetch); the last part's third chunk is loaded here.
     if (t == 0) return;
     const int tp = t - 1;
-    const __nv_bfloat16 *Zt = a.Z + zo + ((size_t)t * B + b) * K0;  // [u_t, h_{t-1}, 0]
-    __nv_bfloat16 *dOp = a.dO + oo + ((size_t)tp * B + b) * N4;
-    const int nch = N4 >> 4, ch0 = (part * nch) / FT_PARTS, ch1 = ((part + 1) * nch) / FT_PARTS;
-    for (int ch = ch0; ch < ch1; ch++) {
-        const int n0 = ch * 16;
-        unsigned r[16];
-        const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)n0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];\n"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int n = n0 + j;
-            if (n >= NIN && n < NIN + NH) {
-                const float h = live ? __bfloat162float(Zt[n]) : 0.0f;
-                const unsigned short hb = bf16_bits(__uint_as_float(r[j]) * (1.0f - h * h));
-                *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NOUT + n - NIN, FT_M)) = hb;
-                if (live) reinterpret_cast<unsigned short *>(dOp)[NOUT + n - NIN] = hb;
-            }
-        }
+    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
+    const int c = part * 32;
+    unsigned ra[16], rb[16];
+    uint4 z2[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    tmem_ld16(ra, tq + c);
+    if (part == FT_PARTS - 1 && live) ld_v8(a.Z + zo + ((size_t)t * B + b) * K0 + c + 32, z2[0], z2[1]);
+    tmem_wait16(ra);
+    tmem_ld16(rb, tq + c + 16);
+    wb_dz16(row, c, ra, y[0], y[1], sZA);
+    tmem_wait16(rb);
+    if (part == FT_PARTS - 1) {
+        tmem_ld16(ra, tq + c + 32);
+        wb_dz16(row, c + 16, rb, y[2], y[3], sZA);
+        tmem_wait16(ra);
+        wb_dz16(row, c + 32, ra, z2[0], z2[1], sZA);
+    } else {
+        wb_dz16(row, c + 16, rb, y[2], y[3], sZA);
     }
-    if (part == 0) {  // the stress columns and the padding of dO_{t-1}
-        for (int n = 0; n < NOUT; n++) {
-            const unsigned short v = bf16_bits(live ? wb_stress_grad(a, S, b, tp, n) : 0.0f);
-            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = v;
-            if (live) reinterpret_cast<unsigned short *>(dOp)[n] = v;
-        }
-        for (int n = NOUT + NH; n < K0; n++) {
-            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = 0;
-            if (live) reinterpret_cast<unsigned short *>(dOp)[n] = 0;
-        }
+    if (part == 0) {  // the stress columns and the padding of dO_{t-1}; all loads before any store
+        float g[NOUT];
+#pragma unroll
+        for (int n = 0; n < NOUT; n++) g[n] = live ? wb_stress_grad(a, S, b, tp, n) : 0.0f;
+#pragma unroll
+        for (int n = 0; n < NOUT; n++) *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = bf16_bits(g[n]);
+        for (int n = NOUT + NH; n < K0; n++) *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = 0;
     }
 }
 
@@ -1174,23 +1319,34 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
         for (int idx = etid; idx < FT_M * K0; idx += nthr) {
             const int r = idx / K0, n = idx - r * K0, b = m0 + r;
             const float v = (n < NOUT && b < a.B) ? wb_stress_grad(a, S, b, T - 1, n) : 0.0f;
-            const unsigned short hv = bf16_bits(v);
-            *reinterpret_cast<unsigned short *>(sZA + cm_off(r, n, FT_M)) = hv;
-            if (b < a.B) reinterpret_cast<unsigned short *>(a.dO + oo)[((size_t)(T - 1) * a.B + b) * N4 + n] = hv;
+            *reinterpret_cast<unsigned short *>(sZA + cm_off(r, n, FT_M)) = bf16_bits(v);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+        // dO rows to global memory: after the initial build and after every dZ
+        // epilogue the hand-over barrier completes a phase of parity 0 (phase 4 i + 4)
+        ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+        if (ok) ws_tape_rows(a.dO + oo + (size_t)(T - 1) * a.B * N4, a.B, sZA, m0, quarter, part, lane);
+        __syncwarp();
         for (int i = 0; i < T && ok; i++)
             for (int l = 0; l < 4 && ok; l++) {
+                const int t = T - 1 - i;
+                uint4 y[4];
+                wb_prefetch(a, yo, zo, l, t, part, m0 + quarter * 32 + lane, y);
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((i * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                wb_epilogue(a, zo, yo, oo, l, T - 1 - i, quarter, part, lane, tmem, sZA, S, m0);
+                wb_epilogue(a, zo, yo, oo, l, t, quarter, part, lane, tmem, sZA, S, m0, y);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
+                if (l == 3 && t > 0) {
+                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+                    if (ok) ws_tape_rows(a.dO + oo + (size_t)(t - 1) * a.B * N4, a.B, sZA, m0, quarter, part, lane);
+                    __syncwarp();
+                }
             }
         if (!ok && lane == 0) atomicExch(a.err, RC_ETIMEOUT);
     }
