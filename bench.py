@@ -192,14 +192,19 @@ NECK_INC, NECK_STRAIN, NECK_MD, NECK_AVG = 150, 0.6, 1000, 500
 NECK_IMPERFECTION = 0.05
 NECK_WORKLOAD = "necking_bar_kg_512x20000"
 NECK_SKINS, NECK_TPAS = (0.4, 0.5, 0.6, 0.7), (0, 1)  # lanes per atom 0: the lean walk
+# the KG bar's uneven batch (761 300 beads, under a tenth of the necking bar)
+# fills fewer warps per SM, so its search also offers the smallest skin and
+# two lanes per bead
+KG_BAR_SKINS, KG_BAR_TPAS = (0.3, 0.4, 0.5, 0.6, 0.8), (0, 1, 2)
 NECK_TUNE_CELLS = 128  # a quarter of the bar: 20 000 tiles, enough waves to behave like the whole
 
 # DRAM bytes (read + write) per bead of one k_force<KG> launch (the lean walk,
 # non-sampling variant), by Verlet skin, from ncu captures of 16 necking-bar
-# cells (320 000 beads): skin 0.4: 146.77 + 6.06 MB, skin 0.5: 160.23 + 6.09 MB.
-# A launch's traffic grows in proportion to its beads (lists, positions and
-# velocities are per bead); the list length depends on the skin.
-K_FORCE_KG_DRAM_BYTES_PER_ATOM = {0.4: 152.83e6 / 320000, 0.5: 166.32e6 / 320000}
+# cells (320 000 beads; mean of two launches): skin 0.4: 146.78 + 4.62 MB,
+# skin 0.5: 160.24 + 4.51 MB.  A launch's traffic grows in proportion to its
+# beads (lists, positions and velocities are per bead); the list length
+# depends on the skin.
+K_FORCE_KG_DRAM_BYTES_PER_ATOM = {0.4: 151.40e6 / 320000, 0.5: 164.75e6 / 320000}
 
 
 def kg_algorithmic_flops_per_atom_step(rho, bonds_per_atom):
@@ -761,7 +766,7 @@ def run_kg_bar(args):
     # autotuned Verlet skin and lanes per atom (timed on the bar's own cells)
     from paper_1902_09171_gb300 import autotune
     make = lambda skin: rcell.params_kg(skin=skin)  # noqa: E731
-    tuned, hit = autotune.tune(make, eq, stream, skins=NECK_SKINS, tpas=NECK_TPAS, n_steps=400, n_avg=200)
+    tuned, hit = autotune.tune(make, eq, stream, skins=KG_BAR_SKINS, tpas=KG_BAR_TPAS, n_steps=400, n_avg=200)
     ctx = rcell.rcell_create(make(tuned["skin"]), eq, stream=stream)
     rcell.rcell_set_tuning(ctx, int(tuned["tpa"]), 1)
     rcell.rcell_run(ctx, 2000, 0)

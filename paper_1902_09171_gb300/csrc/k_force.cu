@@ -184,8 +184,8 @@ __device__ __forceinline__ void eval_group(const int4 &e, int left, const float4
 // periodic displacement d = x_j(image) - x_i.
 // TPA == 0 is the lean walk: one lane per atom, one group at a time with no
 // pipelining -- fewer registers, so that more warps per SM hide the latency
-// instead (the kernels are compiled for 12 resident CTAs then), which pays
-// when the batch has enough tiles to fill them.
+// instead (the force kernel is compiled for 10 resident CTAs then, the density
+// kernel for 12), which pays when the batch has enough tiles to fill them.
 template <int TPA, class Src, class Fn>
 __device__ __forceinline__ void for_each_neighbor(const int4 *__restrict__ nb4, int nn, int sub, const Src &src,
                                                   const float4 &xi, const ShiftTab &T, Fn &&fn) {
@@ -349,12 +349,15 @@ __device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *dst) {
 // Resident CTAs per SM the force kernel is compiled for at one lane per atom
 // (caps its registers at 65536 / (128 * RC_FORCE_MIN_CTAS)).  7 keeps a
 // 128 000-atom batch (1000 tiles) in one wave on 152 SMs; 1 leaves the
-// register count to the compiler.
+// register count to the compiler.  The lean walk takes 10 (48 registers): on
+// the 80 000 tiles of a 10.24 M-bead batch, 12 (40 registers, with spills) ran
+// the force step 3 % and the sampling step 7 % slower, 8 and 9 (no spills)
+// 4-6 % and 1-3 % slower.
 #ifndef RC_FORCE_MIN_CTAS
 #define RC_FORCE_MIN_CTAS 7
 #endif
 constexpr int force_min_ctas(int tpa) {
-    return tpa == 0 ? 12 : (RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1);
+    return tpa == 0 ? 10 : (RC_FORCE_MIN_CTAS / tpa > 0 ? RC_FORCE_MIN_CTAS / tpa : 1);
 }
 
 // SAMPLE: this launch records a stress sample (slot >= 0) or evaluates the

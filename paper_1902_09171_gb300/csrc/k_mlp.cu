@@ -410,34 +410,44 @@ void prepare_tc05() {
 // The whole recurrent forward in one kernel (tcgen05).  A CTA owns 128 rows of
 // the batch (one member: blockIdx.y) and walks all T steps: per step the four
 // layers run back to back on the tensor cores, with the activations kept in
-// shared memory (BF16, K-major core-matrix layout) and the layer accumulator
-// (128 x 256 FP32) in tensor memory.  The roles are split between warps:
-// one producer thread streams the weights through four shared buffers of 64
-// rows each with bulk copies (cp.async.bulk, one per chunk, completing on a
-// per-buffer mbarrier; the weights are pre-arranged per member by
+// shared memory (BF16, K-major core-matrix layout) and the layer accumulators
+// (128 x 256 FP32) in tensor memory, two of them (512 columns), so that a
+// layer's MMAs can write one while the epilogue still reads the other.  The
+// roles are split between warps: one producer thread streams the weights
+// through four shared buffers, one 64-column K slice of a layer (all its output
+// rows) per buffer, with bulk copies (cp.async.bulk, one per chunk, completing
+// on a per-buffer mbarrier; the weights are pre-arranged per member by
 // k_pack_weights so that each chunk is one contiguous block in the buffer's
-// layout) and issues the MMAs; sixteen epilogue warps (warp w: accumulator
-// rows 32 (w % 4).., column quarter w / 4) wait for a layer's accumulator, run
-// its epilogue (bias + GELU into the next operand; the head writes the stress
-// and the new state h = tanh(.) straight into the next step's input rows) and
-// hand the operand back.  The two sides meet only at mbarriers, all waits
-// bounded:
+// layout), and issues the MMAs slice by slice; sixteen epilogue warps (warp w:
+// accumulator rows 32 (w % 4).., columns 16 (w / 4).. of every slice) wait for
+// a layer's accumulator and run its epilogue (bias + GELU into the next
+// operand, slice after slice; the head writes the stress and the new state
+// h = tanh(.) straight into the next step's input rows).  The MMAs of slice s
+// of the next layer start as soon as all warps have written slice s of its
+// operand, under the rest of the epilogue.  The two sides meet only at
+// mbarriers, all waits bounded:
 //   full[b]  : chunk in buffer b has landed          (bulk copy -> producer)
 //   empty[b] : the MMAs reading buffer b are done     (tcgen05.commit -> producer)
 //   acc      : a layer's accumulator is complete      (tcgen05.commit -> epilogue)
-//   epi      : the epilogue warps have written the next operand and read the
-//              accumulator (16 warp arrivals -> producer)
+//   slice[s] : the epilogue warps have written slice s of a hidden layer's
+//              output (16 warp arrivals -> producer)
+//   epi      : the epilogue warps have written the next step's input rows
+//              (16 warp arrivals -> producer, and -> the epilogue warps
+//              before they copy the rows to the tape)
 // With a tape (training) every step's z, y and a rows also go to global memory
 // for the backward pass, in the layout the layer-wise kernels use.
 // ---------------------------------------------------------------------------
-constexpr int FT_PARTS = 4, FT_M = 128, FT_NC = 64, FT_MAXK = 8;
+constexpr int FT_PARTS = 4, FT_M = 128, FT_MAXK = 8;
 // The input rows z (128 x 144) and the activations (128 x 256) share one
 // buffer: z is dead once layer 1's MMAs have read it, and the head writes the
 // next step's state after the last layer's MMAs have read the activations.
-constexpr int FT_NBUF = 4;  // weight buffers
-constexpr int FT_SA = FT_M * WID * 2, FT_SW = FT_NC * WID * 2;
+constexpr int FT_NBUF = 4;   // weight buffers
+constexpr int FT_KS = 64;    // K columns of a weight chunk: one 64-column slice of the layer's operand
+constexpr int FT_SA = FT_M * WID * 2, FT_SW = WID * FT_KS * 2;
 constexpr int FT_SMEM = FT_SA + FT_NBUF * FT_SW;
-constexpr int FT_CHUNKS = 4 + 4 + 4 + 3;  // weight chunks of 64 rows per step (N = 256, 256, 256, 144)
+constexpr int FT_CHUNKS = 3 + 4 + 4 + 4;  // weight chunks per step: K slices of the four layers (K = 144, 256, 256, 256)
+constexpr int FT_TMEM_COLS = 2 * WID;     // two accumulators: layer l uses columns (l % 2) * 256 ..
+static_assert(FT_KS * 4 == WID && FT_KS * 2 < K0 && K0 <= FT_KS * 3, "slices per layer: 3 (K0) or 4 (WID)");
 
 struct FusedArgs {
     const float *U;      // (B, T, NIN) raw features (row b, step t at (b * T + t) * NIN)
@@ -499,36 +509,45 @@ __device__ __forceinline__ float gelu_as(float x) {
 }
 
 constexpr int WS_EPI_WARPS = 16, WS_THREADS = (WS_EPI_WARPS + 1) * 32;
-constexpr int WS_CH0 = FT_NC * K0 * 2, WS_CH1 = FT_NC * WID * 2;  // chunk bytes of layer 1 / layers 2-4
-constexpr int WS_WP_BYTES = 4 * WS_CH0 + 11 * WS_CH1;              // packed weights per member
 static_assert(WS_EPI_WARPS == 4 * FT_PARTS, "epilogue warps cover 4 lane quarters x FT_PARTS column parts");
 
-// byte offset and size of chunk j (0..14) of one step's weight sequence
-__host__ __device__ __forceinline__ int ws_chunk_off(int j) { return j < 4 ? j * WS_CH0 : 4 * WS_CH0 + (j - 4) * WS_CH1; }
-__host__ __device__ __forceinline__ int ws_chunk_bytes(int j) { return j < 4 ? WS_CH0 : WS_CH1; }
+// Chunk j (0..14) of one step's weight sequence: layer l, K slice s (columns
+// 64 s .. 64 s + kw - 1 of the layer's input), all N output rows of the layer:
+// layer 1 (K = 144) in slices of 64, 64 and 16 columns, the others (K = 256)
+// in four of 64; N = 256 for the hidden layers and 144 for the head.
+__host__ __device__ constexpr int ws_chunk_layer(int j) { return j < 3 ? 0 : (j - 3) / 4 + 1; }
+__host__ __device__ constexpr int ws_chunk_slice(int j) { return j < 3 ? j : (j - 3) % 4; }
+__host__ __device__ constexpr int ws_layer_n(int l) { return l == 3 ? N4 : WID; }
+__host__ __device__ constexpr int ws_slice_kw(int l, int sl) {
+    return (l == 0 ? K0 : WID) - sl * FT_KS < FT_KS ? (l == 0 ? K0 : WID) - sl * FT_KS : FT_KS;
+}
+__host__ __device__ constexpr int ws_chunk_bytes(int j) {
+    return ws_layer_n(ws_chunk_layer(j)) * ws_slice_kw(ws_chunk_layer(j), ws_chunk_slice(j)) * 2;
+}
+__host__ __device__ constexpr int ws_chunk_off(int j) { return j == 0 ? 0 : ws_chunk_off(j - 1) + ws_chunk_bytes(j - 1); }
+constexpr int WS_WP_BYTES = ws_chunk_off(FT_CHUNKS);  // packed weights per member
+static_assert(WS_WP_BYTES == (K0 * WID + 2 * WID * WID + WID * N4) * 2, "every weight once");
+static_assert(ws_chunk_bytes(0) <= FT_SW && ws_chunk_bytes(3) <= FT_SW && ws_chunk_bytes(11) <= FT_SW, "chunk fits");
 
-// Wt (N x K row-major, per layer) -> the 15 chunk images, zero rows past N
+// Wt (N x K row-major, per layer) -> the 15 chunk images: chunk j holds
+// element (n, k) of its layer at cm_off(n, k - 64 s, N), the K-major
+// core-matrix layout of an N-row operand with kw columns.
 __global__ void k_pack_weights(const __nv_bfloat16 *__restrict__ W0, const __nv_bfloat16 *__restrict__ W1,
                                const __nv_bfloat16 *__restrict__ W2, const __nv_bfloat16 *__restrict__ W3,
                                unsigned char *Wp) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte unit
-    const int u0 = 4 * FT_NC * (K0 / 8);                   // units of the layer-1 chunks
-    if (u >= u0 + 11 * FT_NC * (WID / 8)) return;
-    int j, idx;
-    if (u < u0) {
-        j = u / (FT_NC * (K0 / 8));
-        idx = u - j * FT_NC * (K0 / 8);
-    } else {
-        j = 4 + (u - u0) / (FT_NC * (WID / 8));
-        idx = (u - u0) - (j - 4) * FT_NC * (WID / 8);
+    int u = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte unit (8 columns of one row)
+    if (u >= WS_WP_BYTES / 16) return;
+    int j = 0;
+    while (u >= ws_chunk_bytes(j) / 16) {
+        u -= ws_chunk_bytes(j) / 16;
+        j++;
     }
-    const int l = j < 4 ? 0 : (j < 8 ? 1 : (j < 12 ? 2 : 3)), q = j - 4 * l;
-    const int K = l == 0 ? K0 : WID, N = l == 3 ? N4 : WID, KC = K / 8;
+    const int l = ws_chunk_layer(j), sl = ws_chunk_slice(j), kw = ws_slice_kw(l, sl);
+    const int K = l == 0 ? K0 : WID, N = ws_layer_n(l), KC = kw / 8;
     const __nv_bfloat16 *Wt = l == 0 ? W0 : (l == 1 ? W1 : (l == 2 ? W2 : W3));
-    const int r = idx / KC, kc = idx - r * KC, n = q * FT_NC + r;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (n < N) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)n * K + kc * 8);
-    *reinterpret_cast<uint4 *>(Wp + ws_chunk_off(j) + cm_off(r, kc * 8, FT_NC)) = v;
+    const int n = u / KC, kc = u - n * KC;
+    const uint4 v = *reinterpret_cast<const uint4 *>(Wt + (size_t)n * K + sl * FT_KS + kc * 8);
+    *reinterpret_cast<uint4 *>(Wp + ws_chunk_off(j) + cm_off(n, kc * 8, N)) = v;
 }
 
 // Bounded wait that lets the hardware park the thread (up to WS_SUSPEND_NS per
@@ -595,17 +614,16 @@ __device__ __forceinline__ void ws_build_h0(const FusedArgs &a, unsigned char *s
 // every epilogue warp has arrived on the hand-over barrier, copied to the tape
 // in pieces of 8 columns (16 bytes; 18 pieces a row; row bb of the batch at
 // dst + bb * K0).  Each warp copies the pieces that its own next epilogue
-// overwrites (the rows of its lane quarter, the 8 pieces of its column part),
-// so that no other warp can overwrite a piece before it has been copied.
+// overwrites -- the rows of its lane quarter, columns 64 s + 16 part .. + 15 of
+// each slice s, i.e. pieces 8 s + 2 part and 8 s + 2 part + 1 -- so that no
+// other warp can overwrite a piece before it has been copied.
 __device__ __forceinline__ void ws_tape_rows(__nv_bfloat16 *dst, int B, const unsigned char *sZA, int m0, int quarter,
                                              int part, int lane) {
     constexpr int KG = K0 / 8;
-    static_assert(KG * 8 == K0, "whole pieces per row");
-    const int kg0 = part * 8, npc = min(KG - kg0, 8);
-    if (npc <= 0) return;
-    for (int i = lane; i < 32 * npc; i += 32) {
-        const int r = quarter * 32 + i / npc, kg = kg0 + i % npc, bb = m0 + r;
-        if (bb < B)
+    static_assert(KG * 8 == K0 && KG <= 3 * 8, "whole pieces per row, in three slices");
+    for (int i = lane; i < 32 * 6; i += 32) {  // 32 rows x (3 slices x 2 pieces)
+        const int r = quarter * 32 + i / 6, e = i % 6, kg = 8 * (e >> 1) + 2 * part + (e & 1), bb = m0 + r;
+        if (kg < KG && bb < B)
             *reinterpret_cast<uint4 *>(dst + (size_t)bb * K0 + kg * 8) =
                 *reinterpret_cast<const uint4 *>(sZA + cm_off(r, kg * 8, FT_M));
     }
@@ -679,36 +697,58 @@ __device__ __forceinline__ void ws_head16(const FusedArgs &a, int t, int row, in
     }
 }
 
-// Epilogue of layer l at step t for one warp: its 32 accumulator rows (lane
-// quarter) and its column part, 16 columns at a time, with the load of the next
-// 16 columns from tensor memory in flight while the current ones are processed
-// (two register sets, straight-line code: no register that a load is still
-// filling is copied or read before its wait).
+// Hands the epilogue's operand writes to the producer: shared-memory writes
+// made visible to the tensor core's proxy, tensor-memory reads ordered before
+// the synchronisation, then one arrival per warp on `bar`.
+__device__ __forceinline__ void ws_hand_over(unsigned bar, int lane) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Epilogue of hidden layer l < 3 at step t for one warp: its 32 accumulator
+// rows (lane quarter), 16 columns in each of the four 64-column slices (column
+// part * 16 of the slice), slice by slice, handing each slice of the next
+// operand over on `slice[s]` as soon as the sixteen warps have written it.  The
+// load of the next 16 columns from tensor memory is in flight while the current
+// ones are processed (two register sets, straight-line code: no register that
+// a load is still filling is copied or read before its wait).
 static_assert(WID / 16 == 4 * FT_PARTS, "a hidden layer's part is four 16-column chunks");
 static_assert(N4 / 16 == 9 && FT_PARTS == 4, "the head's parts are 2, 2, 2 and 3 chunks");
 static_assert(N4 == K0, "the head's output rows and the input rows have the same width");
-__device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tyo, int l, int t, int quarter,
-                                            int part, int lane, unsigned tmem, unsigned char *sZA,
-                                            const float *s_bias, float *S, float *h, int m0) {
-    const int row = quarter * 32 + lane, b = m0 + row;
-    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
+__device__ __forceinline__ void ws_epilogue_hidden(const FusedArgs &a, long tyo, int l, int t, int quarter, int part,
+                                                   int lane, unsigned tmem, unsigned char *sZA, const float *s_bias,
+                                                   unsigned bar_slice, int m0) {
+    const int row = quarter * 32 + lane, b = m0 + row, c = part * 16;
+    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((l & 1) * WID) + (unsigned)c;
     unsigned ra[16], rb[16];
-    if (l < 3) {
-        const int c = part * 64;
-        tmem_ld16(ra, tq + c);
-        tmem_wait16(ra);
-        tmem_ld16(rb, tq + c + 16);
-        ws_act16(a, tyo, l, t, row, b, c, ra, sZA, s_bias);
-        tmem_wait16(rb);
-        tmem_ld16(ra, tq + c + 32);
-        ws_act16(a, tyo, l, t, row, b, c + 16, rb, sZA, s_bias);
-        tmem_wait16(ra);
-        tmem_ld16(rb, tq + c + 48);
-        ws_act16(a, tyo, l, t, row, b, c + 32, ra, sZA, s_bias);
-        tmem_wait16(rb);
-        ws_act16(a, tyo, l, t, row, b, c + 48, rb, sZA, s_bias);
-        return;
-    }
+    tmem_ld16(ra, tq);
+    tmem_wait16(ra);
+    tmem_ld16(rb, tq + FT_KS);
+    ws_act16(a, tyo, l, t, row, b, c, ra, sZA, s_bias);
+    ws_hand_over(bar_slice, lane);
+    tmem_wait16(rb);
+    tmem_ld16(ra, tq + 2 * FT_KS);
+    ws_act16(a, tyo, l, t, row, b, FT_KS + c, rb, sZA, s_bias);
+    ws_hand_over(bar_slice + 8u, lane);
+    tmem_wait16(ra);
+    tmem_ld16(rb, tq + 3 * FT_KS);
+    ws_act16(a, tyo, l, t, row, b, 2 * FT_KS + c, ra, sZA, s_bias);
+    ws_hand_over(bar_slice + 16u, lane);
+    tmem_wait16(rb);
+    ws_act16(a, tyo, l, t, row, b, 3 * FT_KS + c, rb, sZA, s_bias);
+    ws_hand_over(bar_slice + 24u, lane);
+}
+
+// Epilogue of the head at step t for one warp: its lane quarter, the 2, 2, 2
+// or 3 16-column chunks of its part (the accumulator of layer 3: columns 256 ..)
+__device__ __forceinline__ void ws_epilogue_head(const FusedArgs &a, int t, int quarter, int part, int lane,
+                                                 unsigned tmem, unsigned char *sZA, const float *s_bias, float *S,
+                                                 float *h, int m0) {
+    const int row = quarter * 32 + lane, b = m0 + row;
+    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)WID;
+    unsigned ra[16], rb[16];
     const int c = part * 32;  // chunks 2 part, 2 part + 1 (and 8 for the last part)
     tmem_ld16(ra, tq + c);
     tmem_wait16(ra);
@@ -726,38 +766,51 @@ __device__ __forceinline__ void ws_epilogue(const FusedArgs &a, long tyo, int l,
 }
 
 // The producer thread of the warp-specialised kernels: streams T x FT_CHUNKS
-// weight chunks (per step four layers of 4, 4, 4 and 3 chunks of 64 rows; K =
-// K0 for the first layer, WID for the others) through the FT_NBUF buffers and
-// issues each layer's MMAs (A operand in sZA, accumulator columns 64 q ..) as
-// soon as the epilogue warps have handed the operand over.  False on a timeout.
+// weight chunks (per step the K slices of the four layers, see ws_chunk_*)
+// through the FT_NBUF buffers and issues the MMAs slice by slice: slice s of
+// layer l (its K columns 64 s ..) goes as soon as its operand columns are in
+// place -- for the first layer when the whole input rows are (the `epi`
+// barrier), for the others when the epilogue warps have finished slice s of
+// the previous layer (`slice[s]`) -- so that the MMAs of a layer run under
+// the epilogue of the previous one.  Layer l accumulates into tensor-memory
+// columns (l % 2) * 256 .., the other half from the epilogue still reading the
+// previous layer.  False on a timeout.
 __device__ __forceinline__ bool ws_produce(const unsigned char *Wp, int T, unsigned char *sZA, unsigned char *sW,
                                            unsigned tmem, unsigned bar_full, unsigned bar_empty, unsigned bar_acc,
-                                           unsigned bar_epi) {
+                                           unsigned bar_epi, unsigned bar_slice) {
     bool ok = true;
     const long n_chunks = (long)T * FT_CHUNKS;
     for (long c0 = 0; c0 < FT_NBUF && c0 < n_chunks; c0++) ws_bulk(sW, Wp, c0, bar_full);
-    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(FT_NC >> 3) << 17) |
-                           ((unsigned)(FT_M >> 4) << 24);
     const unsigned aBase = (unsigned)__cvta_generic_to_shared(sZA);
-    const unsigned lboA = (FT_M / 8) * 128, lboB = (FT_NC / 8) * 128;
+    const unsigned lboA = (FT_M / 8) * 128;
     long c = 0;
     for (int t = 0; t < T && ok; t++)
         for (int l = 0; l < 4 && ok; l++) {
-            // the layer's operand is in place and the accumulator has been read
-            ok = ws_wait(bar_epi, (unsigned)((t * 4 + l) & 1));
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int Kl = l == 0 ? K0 : WID, nq = l == 3 ? 3 : 4;
-            for (int q = 0; q < nq; q++, c++) {
+            const int N = ws_layer_n(l), ns = l == 0 ? 3 : 4;
+            const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+                                   ((unsigned)(FT_M >> 4) << 24);
+            const unsigned lboB = (unsigned)(N / 8) * 128;
+            const unsigned dcol = tmem + (unsigned)((l & 1) * WID);
+            for (int sl = 0; sl < ns && ok; sl++, c++) {
+                // operand columns of slice sl in place: the input rows of step t
+                // (completion t of `epi`), or slice sl of the previous layer's
+                // epilogue (completion 3 t + l - 1 of `slice[sl]`)
+                if (l == 0) {
+                    if (sl == 0) ok = ws_wait(bar_epi, (unsigned)(t & 1));
+                } else {
+                    ok = ws_wait(bar_slice + 8u * sl, (unsigned)((3 * t + l - 1) & 1));
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int b = (int)(c % FT_NBUF);
                 ok = ws_wait(bar_full + 8u * b, (unsigned)((c / FT_NBUF) & 1));
                 if (!ok) break;
                 const unsigned wb = (unsigned)__cvta_generic_to_shared(sW + (size_t)b * FT_SW);
-                const unsigned dcol = tmem + (unsigned)(q * FT_NC);
-                for (int kk = 0; kk < (Kl >> 4); kk++) {
-                    const uint64_t ad = tc_desc(aBase + kk * 2 * lboA, lboA, 128);
+                const int nkk = ws_slice_kw(l, sl) >> 4;
+                for (int kk = 0; kk < nkk; kk++) {
+                    const uint64_t ad = tc_desc(aBase + (sl * (FT_KS / 16) + kk) * 2 * lboA, lboA, 128);
                     const uint64_t bd = tc_desc(wb + kk * 2 * lboB, lboB, 128);
-                    const unsigned acc = kk > 0;
+                    const unsigned acc = (sl > 0 || kk > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
@@ -785,7 +838,7 @@ __device__ __forceinline__ bool ws_produce(const unsigned char *Wp, int T, unsig
 
 __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     extern __shared__ __align__(1024) unsigned char ft_smem[];
-    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi;
+    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi, s_slice[4];
     __shared__ unsigned s_tmem;
     __shared__ __align__(16) float s_bias[3 * WID + N4];  // b1, b2, b3, b4
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -799,7 +852,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
 
     if (warp == 0) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(WID)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                     "r"(FT_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -811,6 +865,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     const unsigned bar_empty = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
     const unsigned bar_acc = (unsigned)__cvta_generic_to_shared(&s_acc);
     const unsigned bar_epi = (unsigned)__cvta_generic_to_shared(&s_epi);
+    const unsigned bar_slice = (unsigned)__cvta_generic_to_shared(&s_slice[0]);
     if (tid == 0) {
         for (int i = 0; i < FT_NBUF; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full + 8 * i) : "memory");
@@ -818,6 +873,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_acc) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_epi), "r"(WS_EPI_WARPS) : "memory");
+        for (int i = 0; i < 4; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_slice + 8 * i), "r"(WS_EPI_WARPS)
+                         : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -829,7 +887,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     if (warp == WS_EPI_WARPS) {
         // ---- producer: weight chunks and MMAs (one thread) ----
         if (lane == 0) {
-            ok = ws_produce(a.Wp[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi);
+            ok = ws_produce(a.Wp[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi, bar_slice);
             if (!ok) atomicExch(a.err, RC_ETIMEOUT);
         }
     } else {
@@ -840,11 +898,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
         ws_load_u(a, m0, 0, etid, uv);
         ws_store_u(sZA, etid, uv);
         ws_build_h0(a, sZA, h, m0, etid, nthr);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
-        // z rows to the tape: after the initial build and after every head epilogue
-        // the hand-over barrier completes a phase of parity 0 (phase 4 t + 4)
+        ws_hand_over(bar_epi, lane);
+        // z rows to the tape once all warps have written them: completion 0 of
+        // `epi` (the initial rows), completion t + 1 (after the head of step t)
         if (tape) {
             ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
             if (ok) ws_tape_rows(a.tZ + tzo, a.B, sZA, m0, quarter, part, lane);
@@ -856,14 +912,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((t * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                ws_epilogue(a, tyo, l, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
-                if (l == 3 && t + 1 < T) ws_store_u(sZA, etid, uv);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
-                if (tape && l == 3 && t + 1 < T) {
-                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+                if (l < 3) {
+                    ws_epilogue_hidden(a, tyo, l, t, quarter, part, lane, tmem, sZA, s_bias, bar_slice, m0);
+                    continue;
+                }
+                ws_epilogue_head(a, t, quarter, part, lane, tmem, sZA, s_bias, S, h, m0);
+                if (t + 1 < T) ws_store_u(sZA, etid, uv);
+                ws_hand_over(bar_epi, lane);
+                if (tape && t + 1 < T) {
+                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, (unsigned)((t + 1) & 1)));
                     if (ok) ws_tape_rows(a.tZ + tzo + (size_t)(t + 1) * a.B * K0, a.B, sZA, m0, quarter, part, lane);
                     __syncwarp();
                 }
@@ -874,7 +931,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_forward_ws(FusedArgs a) {
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WID) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FT_TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -1141,27 +1199,28 @@ __device__ __forceinline__ float wb_stress_grad(const BwdArgs &a, const float *S
     return a.gscale * (S[i] - a.Y[i] * a.s_inv[n]);
 }
 
-// Columns c0 .. c0 + 31 of the tape row Y_{3-l} of step t (row b) into
-// registers (zero past the batch).  The first half of a part is loaded before
-// the layer's accumulator is ready, so that the global-memory latency runs
-// under the layer's MMAs; the second half while the first is processed.
+// Columns c0 .. c0 + 15 and c0 + 64 .. c0 + 79 of the tape row Y_{3-l} of
+// step t (row b) into registers (zero past the batch): the warp's 16 columns
+// in two consecutive slices.  The first two slices are loaded before the
+// layer's accumulator is ready, so that the global-memory latency runs under
+// the layer's MMAs; the other two while the first is processed.
 __device__ __forceinline__ void wb_load_y(const BwdArgs &a, long yo, int l, int t, int c0, int b, uint4 (&y)[4]) {
 #pragma unroll
     for (int k = 0; k < 4; k++) y[k] = make_uint4(0u, 0u, 0u, 0u);
     if (l < 3 && b < a.B) {
         const __nv_bfloat16 *Yg = a.Yt[2 - l] + yo + ((size_t)t * a.B + b) * WID + c0;
         ld_v8(Yg, y[0], y[1]);
-        ld_v8(Yg + 16, y[2], y[3]);
+        ld_v8(Yg + FT_KS, y[2], y[3]);
     }
 }
 
 // What the warp's epilogue of product l at step t reads from the tape, loaded
-// before the accumulator is ready: for a hidden layer the first 32 of its 64
-// columns of Y_{3-l}, for dZ columns part * 32 .. part * 32 + 31 of the Z row.
+// before the accumulator is ready: for a hidden layer its columns of the first
+// two slices of Y_{3-l}, for dZ columns part * 32 .. part * 32 + 31 of the Z row.
 __device__ __forceinline__ void wb_prefetch(const BwdArgs &a, long yo, long zo, int l, int t, int part, int b,
                                             uint4 (&y)[4]) {
     if (l < 3) {
-        wb_load_y(a, yo, l, t, part * 64, b, y);
+        wb_load_y(a, yo, l, t, part * 16, b, y);
         return;
     }
 #pragma unroll
@@ -1212,31 +1271,37 @@ __device__ __forceinline__ void wb_dz16(int row, int n0, const unsigned (&r)[16]
 }
 
 // Epilogue of backward product l at step t for one warp (lane quarter, column
-// part); y holds the first 32 columns of the part's tape row (wb_load_y).
-// Hidden layers pipeline the tensor-memory loads as the forward epilogue does.
+// part); y holds what wb_prefetch loaded.  Hidden layers go slice by slice as
+// the forward's do (16 columns of each 64-column slice, each slice handed over
+// on `slice[s]`, the next tensor-memory load in flight); dZ (l = 3, the
+// accumulator in columns 256 ..) by the part's 2, 2, 2 or 3 chunks.
 __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, long oo, int l, int t, int quarter,
                                             int part, int lane, unsigned tmem, unsigned char *sZA, const float *S,
-                                            int m0, const uint4 (&y)[4]) {
+                                            int m0, const uint4 (&y)[4], unsigned bar_slice) {
     const int B = a.B, row = quarter * 32 + lane, b = m0 + row;
     const bool live = b < B;
     if (l < 3) {  // dY_{3-l} = acc * gelu'(Y_{3-l})
-        const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
-        const int c = part * 64;
+        const int c = part * 16;
+        const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((l & 1) * WID) + (unsigned)c;
         unsigned ra[16], rb[16];
         uint4 y2[4];
-        tmem_ld16(ra, tq + c);
-        wb_load_y(a, yo, l, t, c + 32, b, y2);
+        tmem_ld16(ra, tq);
+        wb_load_y(a, yo, l, t, 2 * FT_KS + c, b, y2);
         tmem_wait16(ra);
-        tmem_ld16(rb, tq + c + 16);
+        tmem_ld16(rb, tq + FT_KS);
         wb_dy16(a, yo, l, t, row, b, c, ra, y[0], y[1], sZA);
+        ws_hand_over(bar_slice, lane);
         tmem_wait16(rb);
-        tmem_ld16(ra, tq + c + 32);
-        wb_dy16(a, yo, l, t, row, b, c + 16, rb, y[2], y[3], sZA);
+        tmem_ld16(ra, tq + 2 * FT_KS);
+        wb_dy16(a, yo, l, t, row, b, FT_KS + c, rb, y[2], y[3], sZA);
+        ws_hand_over(bar_slice + 8u, lane);
         tmem_wait16(ra);
-        tmem_ld16(rb, tq + c + 48);
-        wb_dy16(a, yo, l, t, row, b, c + 32, ra, y2[0], y2[1], sZA);
+        tmem_ld16(rb, tq + 3 * FT_KS);
+        wb_dy16(a, yo, l, t, row, b, 2 * FT_KS + c, ra, y2[0], y2[1], sZA);
+        ws_hand_over(bar_slice + 16u, lane);
         tmem_wait16(rb);
-        wb_dy16(a, yo, l, t, row, b, c + 48, rb, y2[2], y2[3], sZA);
+        wb_dy16(a, yo, l, t, row, b, 3 * FT_KS + c, rb, y2[2], y2[3], sZA);
+        ws_hand_over(bar_slice + 24u, lane);
         return;
     }
     // dZ_t -> dO_{t-1}; nothing to hand on after step 0.  y holds columns
@@ -1244,7 +1309,7 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
     // (wb_prefetch); the last part's third chunk is loaded here.
     if (t == 0) return;
     const int tp = t - 1;
-    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16);
+    const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)WID;
     const int c = part * 32;
     unsigned ra[16], rb[16];
     uint4 z2[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
@@ -1274,7 +1339,7 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
 
 __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
     extern __shared__ __align__(1024) unsigned char ft_smem[];
-    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi;
+    __shared__ __align__(8) unsigned long long s_full[FT_NBUF], s_empty[FT_NBUF], s_acc, s_epi, s_slice[4];
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mk = blockIdx.y, m0 = blockIdx.x * FT_M;
@@ -1285,7 +1350,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
 
     if (warp == 0) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_tmem);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(WID)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                     "r"(FT_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -1293,6 +1359,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
     const unsigned bar_empty = (unsigned)__cvta_generic_to_shared(&s_empty[0]);
     const unsigned bar_acc = (unsigned)__cvta_generic_to_shared(&s_acc);
     const unsigned bar_epi = (unsigned)__cvta_generic_to_shared(&s_epi);
+    const unsigned bar_slice = (unsigned)__cvta_generic_to_shared(&s_slice[0]);
     if (tid == 0) {
         for (int i = 0; i < FT_NBUF; i++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full + 8 * i) : "memory");
@@ -1300,6 +1367,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_acc) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_epi), "r"(WS_EPI_WARPS) : "memory");
+        for (int i = 0; i < 4; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_slice + 8 * i), "r"(WS_EPI_WARPS)
+                         : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1310,7 +1380,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
 
     if (warp == WS_EPI_WARPS) {
         if (lane == 0) {
-            ok = ws_produce(a.Wb[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi);
+            ok = ws_produce(a.Wb[mk], T, sZA, sW, tmem, bar_full, bar_empty, bar_acc, bar_epi, bar_slice);
             if (!ok) atomicExch(a.err, RC_ETIMEOUT);
         }
     } else {
@@ -1321,11 +1391,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
             const float v = (n < NOUT && b < a.B) ? wb_stress_grad(a, S, b, T - 1, n) : 0.0f;
             *reinterpret_cast<unsigned short *>(sZA + cm_off(r, n, FT_M)) = bf16_bits(v);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
-        // dO rows to global memory: after the initial build and after every dZ
-        // epilogue the hand-over barrier completes a phase of parity 0 (phase 4 i + 4)
+        ws_hand_over(bar_epi, lane);
+        // dO rows to global memory once all warps have written them: completion
+        // 0 of `epi` (dO_{T-1}), completion i + 1 (after the dZ epilogue of
+        // iteration i, dO_{t-1})
         ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
         if (ok) ws_tape_rows(a.dO + oo + (size_t)(T - 1) * a.B * N4, a.B, sZA, m0, quarter, part, lane);
         __syncwarp();
@@ -1337,13 +1406,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((i * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                wb_epilogue(a, zo, yo, oo, l, t, quarter, part, lane, tmem, sZA, S, m0, y);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_epi) : "memory");
-                if (l == 3 && t > 0) {
-                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
+                wb_epilogue(a, zo, yo, oo, l, t, quarter, part, lane, tmem, sZA, S, m0, y, bar_slice);
+                if (l < 3) continue;  // the hidden epilogues hand their slices over themselves
+                ws_hand_over(bar_epi, lane);
+                if (t > 0) {
+                    ok = __all_sync(0xffffffffu, ws_wait(bar_epi, (unsigned)((i + 1) & 1)));
                     if (ok) ws_tape_rows(a.dO + oo + (size_t)(t - 1) * a.B * N4, a.B, sZA, m0, quarter, part, lane);
                     __syncwarp();
                 }
@@ -1354,7 +1421,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WID) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FT_TMEM_COLS)
+                     : "memory");
     }
 }
 
