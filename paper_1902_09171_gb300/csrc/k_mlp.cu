@@ -495,18 +495,35 @@ __device__ __forceinline__ void ld_v8(const void *p, uint4 &lo, uint4 &hi) {
                  : "l"(p));
 }
 
-// GELU x/2 (1 + erf(x / sqrt 2)) with erf from the rational approximation of
-// Abramowitz & Stegun, Handbook of Mathematical Functions (1964), formula
-// 7.1.26 (|error| <= 1.5e-7 for x >= 0; odd extension), far below the BF16
-// rounding of the stored activations.
-__device__ __forceinline__ float gelu_as(float x) {
-    const float z = fabsf(x) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    const float erf_abs = 1.0f - poly * __expf(-z * z);
-    return 0.5f * x * (1.0f + copysignf(erf_abs, x));
+// GELU in the fused kernels: the tanh approximation of Hendrycks & Gimpel,
+// "Gaussian Error Linear Units" (2016), x/2 (1 + tanh(u)) with
+// u = sqrt(2/pi) (x + 0.044715 x^3), evaluated as x s with the logistic form
+// s = 1 / (1 + 2^(-2 u log2 e)) of the same function (one exponential and one
+// reciprocal on the special-function unit, no cancellation in 1 + tanh for
+// large negative x).  Its largest deviation from x/2 (1 + erf(x / sqrt 2)) is
+// 4.7e-4 (at x = 2.7, a sixteenth of the BF16 rounding of the stored
+// activation there); the derivative's is 8.7e-4.
+constexpr float GT_K0 = 0.7978845608028654f;             // sqrt(2 / pi)
+constexpr float GT_K1 = 0.7978845608028654f * 0.044715f;  // sqrt(2 / pi) 0.044715
+constexpr float GT_L = -2.0f * 1.4426950408889634f;       // -2 log2 e
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// s(x) = (1 + tanh(u)) / 2, the smoothed step of the approximation
+__device__ __forceinline__ float gelu_step(float x) {
+    const float x2 = x * x;
+    return rcp_approx(1.0f + ex2_approx(x * fmaf(GT_L * GT_K1, x2, GT_L * GT_K0)));
+}
+__device__ __forceinline__ float gelu_fast(float x) { return x * gelu_step(x); }
 
 constexpr int WS_EPI_WARPS = 16, WS_THREADS = (WS_EPI_WARPS + 1) * 32;
 static_assert(WS_EPI_WARPS == 4 * FT_PARTS, "epilogue warps cover 4 lane quarters x FT_PARTS column parts");
@@ -666,8 +683,8 @@ __device__ __forceinline__ void ws_act16(const FusedArgs &a, long tyo, int l, in
         const float v2 = __uint_as_float(r[j + 2]) + bv.z, v3 = __uint_as_float(r[j + 3]) + bv.w;
         yp[j >> 1] = bf16x2_bits(v0, v1);
         yp[(j >> 1) + 1] = bf16x2_bits(v2, v3);
-        ap[j >> 1] = bf16x2_bits(gelu_as(v0), gelu_as(v1));
-        ap[(j >> 1) + 1] = bf16x2_bits(gelu_as(v2), gelu_as(v3));
+        ap[j >> 1] = bf16x2_bits(gelu_fast(v0), gelu_fast(v1));
+        ap[(j >> 1) + 1] = bf16x2_bits(gelu_fast(v2), gelu_fast(v3));
     }
     const uint4 a0 = make_uint4(ap[0], ap[1], ap[2], ap[3]), a1 = make_uint4(ap[4], ap[5], ap[6], ap[7]);
     *reinterpret_cast<uint4 *>(sZA + cm_off(row, n0, FT_M)) = a0;
@@ -1165,8 +1182,8 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
 // memory (the next operand) and to global memory (for the weight gradients);
 // after dZ_t they build dO_{t-1} = [gscale (s - y / s_scale), dZ_t(state) *
 // (1 - h_{t-1}^2), 0] from the predictions, the targets and the state row of
-// the tape.  GELU' uses the Abramowitz & Stegun 7.1.26 erf of the forward,
-// whose exp(-x^2/2) is also the Gaussian density term.
+// the tape.  GELU' is the derivative of the forward's tanh approximation
+// (gelu_grad_fast), the function the fused forward evaluates.
 // ---------------------------------------------------------------------------
 struct BwdArgs {
     int B, T;
@@ -1182,14 +1199,11 @@ struct BwdArgs {
     int *err;
 };
 
-__device__ __forceinline__ float gelu_grad_as(float x) {
-    const float z = fabsf(x) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    const float e = __expf(-z * z);  // exp(-x^2 / 2)
-    const float erf_abs = 1.0f - poly * e;
-    return 0.5f * (1.0f + copysignf(erf_abs, x)) + x * e * 0.3989422804014327f;
+// derivative of the fused kernels' GELU: s + x s (1 - s) 2 (sqrt(2/pi) + 3
+// sqrt(2/pi) 0.044715 x^2), with s = gelu_step(x)
+__device__ __forceinline__ float gelu_grad_fast(float x) {
+    const float sx = gelu_step(x);
+    return fmaf(x * sx * (1.0f - sx), 2.0f * fmaf(3.0f * GT_K1, x * x, GT_K0), sx);
 }
 
 // dO of step tp = t - 1 (or T - 1 at the start, with no state part): stress
@@ -1242,8 +1256,8 @@ __device__ __forceinline__ void wb_dy16(const BwdArgs &a, long yo, int l, int t,
 #pragma unroll
     for (int j = 0; j < 8; j++) {
         const __nv_bfloat162 yy = *reinterpret_cast<const __nv_bfloat162 *>(&yw[j]);
-        const float g0 = __uint_as_float(r[2 * j]) * gelu_grad_as(__low2float(yy));
-        const float g1 = __uint_as_float(r[2 * j + 1]) * gelu_grad_as(__high2float(yy));
+        const float g0 = __uint_as_float(r[2 * j]) * gelu_grad_fast(__low2float(yy));
+        const float g1 = __uint_as_float(r[2 * j + 1]) * gelu_grad_fast(__high2float(yy));
         dp[j] = bf16x2_bits(g0, g1);
     }
     const uint4 d0 = make_uint4(dp[0], dp[1], dp[2], dp[3]), d1 = make_uint4(dp[4], dp[5], dp[6], dp[7]);
