@@ -17,7 +17,7 @@
 
 namespace {
 
-constexpr int SORT_THREADS = 1024;
+constexpr int SORT_THREADS = 1024, SORT_BATCH = 2;  // atoms per thread whose loads are issued together
 
 // exclusive scan of s[0..n) in place (n <= RC_MAX_BINS_PER_CELL), returns total
 __device__ int block_exclusive_scan(int *s, int n) {
@@ -91,26 +91,46 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     for (int b = threadIdx.x; b < nbt; b += SORT_THREADS) s_cnt[b] = 0;
     __syncthreads();
 
-    // pass A: wrap, bin, stage a copy of every per-atom array
-    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-        const int g = off + i;
-        float4 x = X[g];
-        float s2 = i22 * x.z, s1 = i11 * x.y + i12 * x.z, s0 = i00 * x.x + i01 * x.y + i02 * x.z;
-        float f0 = floorf(s0), f1 = floorf(s1), f2 = floorf(s2);
-        float w0 = s0 - f0, w1 = s1 - f1, w2 = s2 - f2;
-        float xw = x.x - (h00 * f0 + h01 * f1 + h02 * f2);
-        float yw = x.y - (h11 * f1 + h12 * f2);
-        float zw = x.z - h22 * f2;
-        int b0 = min(max((int)(w0 * nb0), 0), nb0 - 1);
-        int b1 = min(max((int)(w1 * nb1), 0), nb1 - 1);
-        int b2 = min(max((int)(w2 * nb2), 0), nb2 - 1);
-        int bin = (b0 * nb1 + b1) * nb2 + b2;
-        a.x_tmp[g] = make_float4(xw, yw, zw, 0.0f);
-        a.binid[g] = bin;
-        a.v_tmp[g] = a.v[g];
-        a.tag_tmp[g] = a.tag[g];
-        if (kg) a.partner_tmp[g] = a.partner[g];
-        atomicAdd(&s_cnt[bin], 1);
+    // pass A: wrap, bin, stage a copy of every per-atom array; SORT_BATCH atoms
+    // per thread at a time, all their loads issued before any store, so that the
+    // loads overlap (the staging arrays are distinct from the sources)
+    for (int i0 = threadIdx.x; i0 < n; i0 += SORT_THREADS * SORT_BATCH) {
+        float4 xb[SORT_BATCH], vb[SORT_BATCH];
+        int tb[SORT_BATCH];
+        int4 pb[SORT_BATCH];
+#pragma unroll
+        for (int k = 0; k < SORT_BATCH; k++) {
+            const int i = i0 + k * SORT_THREADS;
+            if (i < n) {
+                xb[k] = X[off + i];
+                vb[k] = a.v[off + i];
+                tb[k] = a.tag[off + i];
+                if (kg) pb[k] = a.partner[off + i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SORT_BATCH; k++) {
+            const int i = i0 + k * SORT_THREADS;
+            if (i >= n) break;
+            const int g = off + i;
+            const float4 x = xb[k];
+            float s2 = i22 * x.z, s1 = i11 * x.y + i12 * x.z, s0 = i00 * x.x + i01 * x.y + i02 * x.z;
+            float f0 = floorf(s0), f1 = floorf(s1), f2 = floorf(s2);
+            float w0 = s0 - f0, w1 = s1 - f1, w2 = s2 - f2;
+            float xw = x.x - (h00 * f0 + h01 * f1 + h02 * f2);
+            float yw = x.y - (h11 * f1 + h12 * f2);
+            float zw = x.z - h22 * f2;
+            int b0 = min(max((int)(w0 * nb0), 0), nb0 - 1);
+            int b1 = min(max((int)(w1 * nb1), 0), nb1 - 1);
+            int b2 = min(max((int)(w2 * nb2), 0), nb2 - 1);
+            int bin = (b0 * nb1 + b1) * nb2 + b2;
+            a.x_tmp[g] = make_float4(xw, yw, zw, 0.0f);
+            a.binid[g] = bin;
+            a.v_tmp[g] = vb[k];
+            a.tag_tmp[g] = tb[k];
+            if (kg) a.partner_tmp[g] = pb[k];
+            atomicAdd(&s_cnt[bin], 1);
+        }
     }
     __syncthreads();
 
@@ -154,29 +174,61 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(KParams p, KArrays a, int
     }
     __syncthreads();
 
-    // pass B: scatter into sorted order
-    for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-        const int g = off + i;
-        const int q = off + a.newpos[g];
-        float4 xw = a.x_tmp[g];
-        X[q] = xw;
-        a.xref[q] = xw;
-        a.v[q] = a.v_tmp[g];
-        a.tag[q] = a.tag_tmp[g];
-        a.oldidx[q] = i;
-        a.bin_of[q] = a.binid[g];
+    // pass B: scatter into sorted order (batched like pass A: the staged
+    // arrays are read, the per-atom arrays written)
+    for (int i0 = threadIdx.x; i0 < n; i0 += SORT_THREADS * SORT_BATCH) {
+        int qb[SORT_BATCH], bb[SORT_BATCH], tb[SORT_BATCH];
+        float4 xb[SORT_BATCH], vb[SORT_BATCH];
+#pragma unroll
+        for (int k = 0; k < SORT_BATCH; k++) {
+            const int i = i0 + k * SORT_THREADS;
+            if (i < n) {
+                const int g = off + i;
+                qb[k] = a.newpos[g];
+                xb[k] = a.x_tmp[g];
+                vb[k] = a.v_tmp[g];
+                tb[k] = a.tag_tmp[g];
+                bb[k] = a.binid[g];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SORT_BATCH; k++) {
+            const int i = i0 + k * SORT_THREADS;
+            if (i >= n) break;
+            const int q = off + qb[k];
+            X[q] = xb[k];
+            a.xref[q] = xb[k];
+            a.v[q] = vb[k];
+            a.tag[q] = tb[k];
+            a.oldidx[q] = i;
+            a.bin_of[q] = bb[k];
+        }
     }
     if (kg) {
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += SORT_THREADS) {
-            const int q = off + i;
-            int4 pr = a.partner_tmp[off + a.oldidx[q]];
-            int4 out;
-            out.x = pr.x >= 0 ? a.newpos[off + pr.x] : -1;
-            out.y = pr.y >= 0 ? a.newpos[off + pr.y] : -1;
-            out.z = pr.z >= 0 ? a.newpos[off + pr.z] : -1;
-            out.w = pr.w >= 0 ? a.newpos[off + pr.w] : -1;
-            a.partner[q] = out;
+        // bonded partners renumbered: oldidx, partner_tmp and newpos are read,
+        // partner written
+        for (int i0 = threadIdx.x; i0 < n; i0 += SORT_THREADS * SORT_BATCH) {
+            int4 pb[SORT_BATCH];
+#pragma unroll
+            for (int k = 0; k < SORT_BATCH; k++) {
+                const int i = i0 + k * SORT_THREADS;
+                if (i < n) pb[k] = a.partner_tmp[off + a.oldidx[off + i]];
+            }
+#pragma unroll
+            for (int k = 0; k < SORT_BATCH; k++) {
+                const int i = i0 + k * SORT_THREADS;
+                if (i < n) {
+                    const int4 pr = pb[k];
+                    pb[k] = make_int4(pr.x >= 0 ? a.newpos[off + pr.x] : -1, pr.y >= 0 ? a.newpos[off + pr.y] : -1,
+                                      pr.z >= 0 ? a.newpos[off + pr.z] : -1, pr.w >= 0 ? a.newpos[off + pr.w] : -1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SORT_BATCH; k++) {
+                const int i = i0 + k * SORT_THREADS;
+                if (i < n) a.partner[off + i] = pb[k];
+            }
         }
     }
 }
