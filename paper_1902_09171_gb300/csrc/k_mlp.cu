@@ -696,6 +696,14 @@ __device__ __forceinline__ void ws_act16(const FusedArgs &a, long tyo, int l, in
     }
 }
 
+// tanh on the special-function unit (tanh.approx.f32, maximum relative error
+// about 2^-11, a quarter of the BF16 rounding of the stored state)
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // head layer, columns n0 .. n0 + 15 of row `row`: the stress outputs and the
 // next state (tanh) into the state columns of the next step's input rows
 __device__ __forceinline__ void ws_head16(const FusedArgs &a, int t, int row, int b, int n0, const unsigned (&r)[16],
@@ -707,7 +715,7 @@ __device__ __forceinline__ void ws_head16(const FusedArgs &a, int t, int row, in
         if (n < NOUT) {
             if (b < a.B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
         } else if (n < NOUT + NH) {
-            const float hv = tanhf(o);
+            const float hv = tanh_approx(o);
             *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = bf16_bits(hv);
             if (h && b < a.B && t + 1 == a.T) h[(size_t)b * NH + n - NOUT] = hv;
         }
