@@ -1299,7 +1299,7 @@ __device__ __forceinline__ void wb_dz16(int row, int n0, const unsigned (&r)[16]
 // accumulator in columns 256 ..) by the part's 2, 2, 2 or 3 chunks.
 __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, long oo, int l, int t, int quarter,
                                             int part, int lane, unsigned tmem, unsigned char *sZA, const float *S,
-                                            int m0, const uint4 (&y)[4], unsigned bar_slice) {
+                                            int m0, const uint4 (&y)[4], unsigned bar_slice, const float (&g)[NOUT]) {
     const int B = a.B, row = quarter * 32 + lane, b = m0 + row;
     const bool live = b < B;
     if (l < 3) {  // dY_{3-l} = acc * gelu'(Y_{3-l})
@@ -1330,7 +1330,6 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
     // part * 32 .. part * 32 + 31 of the Z tape row [u_t, h_{t-1}, 0]
     // (wb_prefetch); the last part's third chunk is loaded here.
     if (t == 0) return;
-    const int tp = t - 1;
     const unsigned tq = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)WID;
     const int c = part * 32;
     unsigned ra[16], rb[16];
@@ -1349,10 +1348,7 @@ __device__ __forceinline__ void wb_epilogue(const BwdArgs &a, long zo, long yo, 
     } else {
         wb_dz16(row, c + 16, rb, y[2], y[3], sZA);
     }
-    if (part == 0) {  // the stress columns and the padding of dO_{t-1}; all loads before any store
-        float g[NOUT];
-#pragma unroll
-        for (int n = 0; n < NOUT; n++) g[n] = live ? wb_stress_grad(a, S, b, tp, n) : 0.0f;
+    if (part == 0) {  // the stress columns (g, formed two products earlier) and the padding of dO_{t-1}
 #pragma unroll
         for (int n = 0; n < NOUT; n++) *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = bf16_bits(g[n]);
         for (int n = NOUT + NH; n < K0; n++) *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n, FT_M)) = 0;
@@ -1420,15 +1416,23 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_backward_ws(BwdArgs a) {
         ok = __all_sync(0xffffffffu, ws_wait(bar_epi, 0u));
         if (ok) ws_tape_rows(a.dO + oo + (size_t)(T - 1) * a.B * N4, a.B, sZA, m0, quarter, part, lane);
         __syncwarp();
+        float g[NOUT];  // the part-0 warps' stress gradients of dO_{t-1}, loaded while dY2 and dY1 run
+#pragma unroll
+        for (int n = 0; n < NOUT; n++) g[n] = 0.0f;
         for (int i = 0; i < T && ok; i++)
             for (int l = 0; l < 4 && ok; l++) {
                 const int t = T - 1 - i;
+                if (part == 0 && l == 1 && t > 0) {
+                    const int b = m0 + quarter * 32 + lane;
+#pragma unroll
+                    for (int n = 0; n < NOUT; n++) g[n] = b < a.B ? wb_stress_grad(a, S, b, t - 1, n) : 0.0f;
+                }
                 uint4 y[4];
                 wb_prefetch(a, yo, zo, l, t, part, m0 + quarter * 32 + lane, y);
                 ok = __all_sync(0xffffffffu, ws_wait(bar_acc, (unsigned)((i * 4 + l) & 1)));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                wb_epilogue(a, zo, yo, oo, l, t, quarter, part, lane, tmem, sZA, S, m0, y, bar_slice);
+                wb_epilogue(a, zo, yo, oo, l, t, quarter, part, lane, tmem, sZA, S, m0, y, bar_slice, g);
                 if (l < 3) continue;  // the hidden epilogues hand their slices over themselves
                 ws_hand_over(bar_epi, lane);
                 if (t > 0) {
