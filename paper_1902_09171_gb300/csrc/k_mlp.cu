@@ -696,6 +696,31 @@ __device__ __forceinline__ void ws_act16(const FusedArgs &a, long tyo, int l, in
     }
 }
 
+// State columns of an operand row: value v[j] of accumulator column n0 + j
+// (kept where LO <= n0 + j < LO + NH) goes to operand column n0 + j + SHIFT of
+// row `row`.  The shift is odd and n0 even, so the pairs (j, j + 1) with odd j
+// land on an aligned column pair and go as one 4-byte store; j = 0 and 15 alone.
+template <int LO, int SHIFT>
+__device__ __forceinline__ void st_state16(unsigned char *sZA, int row, int n0, const float (&v)[16]) {
+    static_assert(SHIFT & 1, "odd column shift");
+    const auto ok = [&](int j) { return n0 + j >= LO && n0 + j < LO + NH; };
+    const auto one = [&](int j) {
+        *reinterpret_cast<unsigned short *>(sZA + cm_off(row, n0 + j + SHIFT, FT_M)) = bf16_bits(v[j]);
+    };
+    if (ok(0)) one(0);
+#pragma unroll
+    for (int j = 1; j < 15; j += 2) {
+        const bool a0 = ok(j), a1 = ok(j + 1);
+        if (a0 && a1) {
+            *reinterpret_cast<unsigned *>(sZA + cm_off(row, n0 + j + SHIFT, FT_M)) = bf16x2_bits(v[j], v[j + 1]);
+        } else {
+            if (a0) one(j);
+            if (a1) one(j + 1);
+        }
+    }
+    if (ok(15)) one(15);
+}
+
 // tanh on the special-function unit (tanh.approx.f32, maximum relative error
 // about 2^-11, a quarter of the BF16 rounding of the stored state)
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -708,18 +733,19 @@ __device__ __forceinline__ float tanh_approx(float x) {
 // next state (tanh) into the state columns of the next step's input rows
 __device__ __forceinline__ void ws_head16(const FusedArgs &a, int t, int row, int b, int n0, const unsigned (&r)[16],
                                           unsigned char *sZA, const float *s_bias, float *S, float *h) {
+    float hv[16];
 #pragma unroll
     for (int j = 0; j < 16; j++) {
         const int n = n0 + j;
         const float o = __uint_as_float(r[j]) + s_bias[3 * WID + n];
+        hv[j] = tanh_approx(o);  // used for the state columns only
         if (n < NOUT) {
             if (b < a.B) S[(size_t)b * a.s_ld + t * NOUT + n] = a.s_mul ? o * a.s_mul[n] : o;
         } else if (n < NOUT + NH) {
-            const float hv = tanh_approx(o);
-            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NIN + n - NOUT, FT_M)) = bf16_bits(hv);
-            if (h && b < a.B && t + 1 == a.T) h[(size_t)b * NH + n - NOUT] = hv;
+            if (h && b < a.B && t + 1 == a.T) h[(size_t)b * NH + n - NOUT] = hv[j];
         }
     }
+    st_state16<NOUT, NIN - NOUT>(sZA, row, n0, hv);
 }
 
 // Hands the epilogue's operand writes to the producer: shared-memory writes
@@ -1280,16 +1306,14 @@ __device__ __forceinline__ void wb_dy16(const BwdArgs &a, long yo, int l, int t,
 __device__ __forceinline__ void wb_dz16(int row, int n0, const unsigned (&r)[16], const uint4 &z0, const uint4 &z1,
                                         unsigned char *sZA) {
     const unsigned zw[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+    float v[16];
 #pragma unroll
     for (int j = 0; j < 16; j++) {
-        const int n = n0 + j;
-        if (n >= NIN && n < NIN + NH) {
-            const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(&zw[j >> 1]);
-            const float h = (j & 1) ? __high2float(hh) : __low2float(hh);
-            *reinterpret_cast<unsigned short *>(sZA + cm_off(row, NOUT + n - NIN, FT_M)) =
-                bf16_bits(__uint_as_float(r[j]) * (1.0f - h * h));
-        }
+        const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162 *>(&zw[j >> 1]);
+        const float h = (j & 1) ? __high2float(hh) : __low2float(hh);
+        v[j] = __uint_as_float(r[j]) * (1.0f - h * h);
     }
+    st_state16<NIN, NOUT - NIN>(sZA, row, n0, v);
 }
 
 // Epilogue of backward product l at step t for one warp (lane quarter, column
