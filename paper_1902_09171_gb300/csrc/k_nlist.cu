@@ -309,11 +309,12 @@ __global__ void __launch_bounds__(RC_TILE, 8) k_nlist(KParams p, KArrays a, int 
                         for (int k = 0; k < NBATCH; k++) {
                             const int jl = jb + k;
                             if (jl >= j1) break;
-                            if (jl == li && slot == RC_SLOT_CENTRAL) continue;
-                            if (jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w) continue;
                             const float3 d = rc_disp_pre(xj[k], sa, xs);
                             const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-                            if (r2 < p.rlist2) {
+                            // the atom itself and its bond partners are left out; tested on the
+                            // quarter of the candidates inside r_list only
+                            if (r2 < p.rlist2 && !(jl == li && slot == RC_SLOT_CENTRAL) &&
+                                !(jl == pr.x || jl == pr.y || jl == pr.z || jl == pr.w)) {
                                 if (cnt < p.max_nb)
                                     nbr[(size_t)(cnt >> 2) * (4 * RC_TILE) + (cnt & 3)] =
                                         (int)((unsigned)(off + jl) | ((unsigned)slot << RC_IDX_BITS));
