@@ -1077,9 +1077,9 @@ def run_surrogate_fe(args):
 
 
 def run_surrogate_fe_cu(args):
-    """The learned surrogate against plain r-cell MD on the copper bar: BASELINE's
-    training set of "config-2-style r-cells" read as the copper bar's own
-    Sutton-Chen r-cells (4000 atoms, 300 K).  Data: `--paths` cells driven along
+    """The learned surrogate against plain r-cell MD on the copper bar: the
+    surrogate's training set of copper-bar-style r-cells read as the copper bar's
+    own Sutton-Chen r-cells (4000 atoms, 300 K).  Data: `--paths` cells driven along
     seeded bar-like deformation histories (25 increments, --sur-md MD steps each,
     stress averaged over the second half) through the batched r-cell engine;
     BF16 training of a 4-member ensemble on 90 % of them; then the copper bar's
